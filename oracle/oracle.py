@@ -1,0 +1,207 @@
+"""ctypes binding of ``parcels_oracle.c`` (test infrastructure only).
+
+The oracle follows Eq. 1 and Sect. 2.1.1, 2.1.2, 2.3, 2.4 and 4.2 of
+Lange & van Sebille, "Parcels v0.9" (arXiv 1707.05163).  The C file's header
+lists every reading taken where the paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "parcels_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "libparcels_oracle.so")
+
+ALIVE, OOB_HORIZ, OOB_DEPTH, NAN = 0, 1, 2, 3
+BROWNIAN, SINK = 1, 2
+EULER, RK4 = 0, 1
+FLAT, SPHERICAL = 0, 1
+DEG_M = 1852.0 * 60.0
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".{os.getpid()}.tmp"
+        subprocess.check_call([
+            "gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+            "-shared", "-pthread", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+class _FieldSet(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("lon", C.c_void_p), ("lat", C.c_void_p), ("depth", C.c_void_p),
+        ("mesh", C.c_int), ("periodic_lon", C.c_int), ("nfields", C.c_int),
+        ("nt", C.c_int), ("times", C.c_void_p), ("period", C.c_double),
+        ("dtype", C.c_int), ("data", C.c_void_p), ("deg_m", C.c_double),
+    ]
+
+
+class _Kernel(C.Structure):
+    _fields_ = [
+        ("scheme", C.c_int), ("behaviours", C.c_uint), ("kh", C.c_double),
+        ("w_sink", C.c_double), ("seed", C.c_uint64),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            dp = C.POINTER(C.c_double)
+            ip = C.POINTER(C.c_int)
+            L.or_locate.argtypes = [C.c_void_p, C.c_int, C.c_double, ip, dp]
+            L.or_locate.restype = C.c_int
+            L.or_locate_lon.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, ip, ip, dp]
+            L.or_locate_lon.restype = C.c_int
+            L.or_wrap_lon.argtypes = [C.c_double, C.c_double]
+            L.or_wrap_lon.restype = C.c_double
+            L.or_sample.argtypes = [C.POINTER(_FieldSet), C.c_double, C.c_double, C.c_double,
+                                    C.c_double, dp]
+            L.or_sample.restype = C.c_int
+            L.or_velocity.argtypes = L.or_sample.argtypes
+            L.or_velocity.restype = C.c_int
+            L.or_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            L.or_philox4x32_10.restype = None
+            L.or_normal_pair.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, dp, dp]
+            L.or_normal_pair.restype = None
+            L.or_run.argtypes = [C.POINTER(_FieldSet), C.POINTER(_Kernel), C.c_int64] + \
+                [C.c_void_p] * 7 + [C.c_double, C.c_double, C.c_double, C.c_int]
+            L.or_run.restype = C.c_int64
+            L.or_quantise.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_void_p]
+            L.or_quantise.restype = C.c_float
+            L.or_dequantise.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_float, C.c_void_p]
+            L.or_dequantise.restype = None
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class Field:
+    """A rectilinear field set: axes, snapshots and the snapshot data.
+
+    ``data`` has shape (nt, nfields, nz, ny, nx), float64 or float32, lon
+    fastest.  ``period`` > 0 makes the field repeat in time with that period.
+    """
+
+    def __init__(self, lon, lat, depth, times, data, mesh=FLAT, periodic_lon=False,
+                 period=0.0, deg_m=DEG_M):
+        self.lon = np.ascontiguousarray(lon, dtype=np.float64)
+        self.lat = np.ascontiguousarray(lat, dtype=np.float64)
+        self.depth = np.ascontiguousarray(np.atleast_1d(depth), dtype=np.float64)
+        self.times = np.ascontiguousarray(np.atleast_1d(times), dtype=np.float64)
+        if data.dtype not in (np.float64, np.float32):
+            data = data.astype(np.float64)
+        self.data = np.ascontiguousarray(data)
+        nt, nf, nz, ny, nx = self.data.shape
+        assert (nt, nz, ny, nx) == (len(self.times), len(self.depth), len(self.lat), len(self.lon))
+        assert nf in (2, 3)
+        self.s = _FieldSet(nx, ny, nz, _ptr(self.lon), _ptr(self.lat), _ptr(self.depth),
+                           int(mesh), int(bool(periodic_lon)), nf, nt, _ptr(self.times),
+                           float(period), 0 if self.data.dtype == np.float64 else 1,
+                           _ptr(self.data), float(deg_m))
+
+
+class Kernel:
+    def __init__(self, scheme=RK4, behaviours=0, kh=0.0, w_sink=0.0, seed=0):
+        self.k = _Kernel(int(scheme), int(behaviours), float(kh), float(w_sink), int(seed))
+
+
+def run(field: Field, kernel: Kernel, lon, lat, depth, time, ids, step, status, dt,
+        t_stop, t_end=None, nthreads=None):
+    """Advance particles in place (arrays: float64 x4, uint64, uint32, uint8).
+
+    Every live particle steps while its time is before ``t_stop`` and before
+    ``t_end`` (in the direction of dt); the last step is shortened to land on
+    ``t_end``.  Returns the number of particle-steps taken.
+    """
+    if t_end is None:
+        t_end = t_stop
+    if nthreads is None:
+        nthreads = len(os.sched_getaffinity(0))
+    for a, dt_ in ((lon, np.float64), (lat, np.float64), (depth, np.float64),
+                   (time, np.float64), (ids, np.uint64), (step, np.uint32), (status, np.uint8)):
+        assert a.dtype == dt_ and a.flags.c_contiguous
+    n = len(lon)
+    r = lib().or_run(C.byref(field.s), C.byref(kernel.k), n, _ptr(lon), _ptr(lat), _ptr(depth),
+                     _ptr(time), _ptr(ids), _ptr(step), _ptr(status), float(dt), float(t_stop),
+                     float(t_end), int(nthreads))
+    if r < 0:
+        raise ValueError("time span outside the field's time range")
+    return int(r)
+
+
+def sample(field: Field, t, lon, lat, depth=0.0):
+    out = (C.c_double * 3)()
+    r = lib().or_sample(C.byref(field.s), t, lon, lat, depth, out)
+    return r, np.array(out[:field.data.shape[1]])
+
+
+def velocity(field: Field, t, lon, lat, depth=0.0):
+    out = (C.c_double * 3)()
+    r = lib().or_velocity(C.byref(field.s), t, lon, lat, depth, out)
+    return r, np.array(out[:3])
+
+
+def locate(x, p):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    i, xi = C.c_int(), C.c_double()
+    r = lib().or_locate(_ptr(x), len(x), float(p), C.byref(i), C.byref(xi))
+    return r, i.value, xi.value
+
+
+def locate_lon(x, p, periodic=True):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    i0, i1, xi = C.c_int(), C.c_int(), C.c_double()
+    r = lib().or_locate_lon(_ptr(x), len(x), int(periodic), float(p), C.byref(i0),
+                            C.byref(i1), C.byref(xi))
+    return r, i0.value, i1.value, xi.value
+
+
+def wrap_lon(p, x0):
+    return lib().or_wrap_lon(float(p), float(x0))
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().or_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def normal_pair(seed, pid, step):
+    a, b = C.c_double(), C.c_double()
+    lib().or_normal_pair(int(seed), int(pid), int(step), C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def quantise(v, kind):
+    """kind 0: binary16, 1: bfloat16.  Returns (uint16 codes, float32 scale)."""
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    q = np.empty(v.shape, dtype=np.uint16)
+    s = lib().or_quantise(_ptr(v), v.size, int(kind), _ptr(q))
+    return q, np.float32(s)
+
+
+def dequantise(q, kind, scale):
+    q = np.ascontiguousarray(q, dtype=np.uint16)
+    out = np.empty(q.shape, dtype=np.float64)
+    lib().or_dequantise(_ptr(q), q.size, int(kind), float(scale), _ptr(out))
+    return out

@@ -1,0 +1,457 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle.
+
+Each test checks the oracle against a closed form, a library routine, an
+invariant or a number the paper prints (Sect. 4.2), chosen so that a dropped
+term, a wrong sign, a swapped index or a wrong stage time fails one of them.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+DAY = 86400.0
+
+
+def _state(lon, lat, depth=None, t0=0.0, ids=None):
+    n = len(lon)
+    lon = np.array(lon, dtype=np.float64)
+    lat = np.array(lat, dtype=np.float64)
+    depth = np.zeros(n) if depth is None else np.array(depth, dtype=np.float64)
+    time = np.full(n, t0, dtype=np.float64)
+    ids = np.arange(n, dtype=np.uint64) if ids is None else np.asarray(ids, dtype=np.uint64)
+    return dict(lon=lon, lat=lat, depth=depth, time=time, ids=ids,
+                step=np.zeros(n, dtype=np.uint32), status=np.zeros(n, dtype=np.uint8))
+
+
+def _field(spec):
+    return O.Field(spec.lon, spec.lat, spec.depth, spec.times, spec.data, spec.mesh,
+                   spec.periodic_lon, spec.period)
+
+
+def _run(field, kernel, st, dt, t_stop, t_end=None):
+    return O.run(field, kernel, st["lon"], st["lat"], st["depth"], st["time"], st["ids"],
+                 st["step"], st["status"], dt, t_stop, t_end)
+
+
+# --------------------------------------------------------------------------
+# Cell search: pinned to numpy.searchsorted (a library routine).
+# --------------------------------------------------------------------------
+
+def test_locate_matches_searchsorted():
+    rng = np.random.default_rng(11)
+    for n in (2, 3, 7, 50, 1441):
+        x = np.cumsum(rng.uniform(0.1, 2.0, n))
+        ps = np.concatenate([rng.uniform(x[0], x[-1], 300), x, [x[0], x[-1]]])
+        for p in ps:
+            r, i, xi = O.locate(x, p)
+            assert r == 0
+            ref = min(int(np.searchsorted(x, p, side="right")) - 1, n - 2)
+            assert i == ref
+            assert 0.0 <= xi <= 1.0
+            assert abs(x[i] + xi * (x[i + 1] - x[i]) - p) <= 1e-12 * max(1.0, abs(p))
+        for p in (x[0] - 1e-9, x[-1] + 1e-9, np.nan):
+            assert O.locate(x, p)[0] == 1
+    # last node belongs to the last cell with xi = 1
+    x = np.array([0.0, 1.0, 3.0])
+    assert O.locate(x, 3.0)[1:] == (1, 1.0)
+    assert O.locate(x, 1.0)[1:] == (1, 0.0)
+    # a single-node axis (the depth axis of a 2-D field)
+    assert O.locate(np.array([0.0]), 0.0) == (0, 0, 0.0)
+
+
+def test_periodic_lon_wrap_and_wrap_cell():
+    lon = np.arange(0.0, 360.0, 0.25)
+    for p, q in ((-0.125, 359.875), (360.0, 0.0), (725.5, 5.5), (-720.0, 0.0)):
+        assert O.wrap_lon(p, 0.0) == q
+    r, i0, i1, xi = O.locate_lon(lon, 359.875)
+    assert (r, i0, i1, xi) == (0, 1439, 0, 0.5)
+    # shifting by whole turns changes nothing (values exact in binary)
+    for p in (0.125, 17.5, 359.9375, 200.0):
+        ref = O.locate_lon(lon, p)
+        for k in (-3, -1, 1, 2):
+            assert O.locate_lon(lon, p + 360.0 * k) == ref
+    # the interpolant of sin(lon) errs by at most h^2/8 max|f''| (linear
+    # interpolation bound), also inside the wrap cell
+    spec = synth.zonal_flow_sphere(res=5.0)
+    lam = np.deg2rad(spec.lon)
+    data = np.zeros((1, 2, 1, len(spec.lat), len(spec.lon)))
+    data[0, 0] = np.sin(lam)[None, :]
+    f = O.Field(spec.lon, spec.lat, spec.depth, spec.times, data, 1, True)
+    h = np.deg2rad(5.0)
+    for p in np.linspace(-30.0, 390.0, 421):
+        r, v = O.sample(f, 0.0, p, 0.0)
+        assert r == 0
+        assert abs(v[0] - np.sin(np.deg2rad(p))) <= h * h / 8 + 1e-12
+
+
+# --------------------------------------------------------------------------
+# Interpolation: exact on fields linear in x, y, z and t.
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nz,nt", [(1, 1), (1, 3), (5, 1), (5, 4)])
+def test_interpolation_exact_for_linear_fields(nz, nt):
+    rng = np.random.default_rng(100 + 10 * nz + nt)
+    spec, coef = synth.linear_field(rng, nz=nz, nt=nt, nfields=3 if nz > 1 else 2)
+    f = _field(spec)
+    for _ in range(400):
+        x = rng.uniform(spec.lon[0], spec.lon[-1])
+        y = rng.uniform(spec.lat[0], spec.lat[-1])
+        z = rng.uniform(spec.depth[0], spec.depth[-1])
+        t = rng.uniform(spec.times[0], spec.times[-1])
+        r, v = O.sample(f, t, x, y, z)
+        assert r == 0
+        zz = z if nz > 1 else spec.depth[0]
+        tt = t if nt > 1 else spec.times[0]
+        ref = coef[:, 0] + coef[:, 1] * x * 1e-3 + coef[:, 2] * y * 1e-3 + \
+            coef[:, 3] * zz * 1e-2 + coef[:, 4] * tt / DAY
+        np.testing.assert_allclose(v, ref[:len(v)], rtol=0, atol=1e-11)
+
+
+def test_nodes_and_snapshots_are_reproduced():
+    rng = np.random.default_rng(5)
+    spec, _ = synth.linear_field(rng, nz=4, nt=3)
+    spec.data = rng.normal(size=spec.data.shape)
+    f = _field(spec)
+    for _ in range(100):
+        i, j, k, s = (rng.integers(0, len(spec.lon)), rng.integers(0, len(spec.lat)),
+                      rng.integers(0, len(spec.depth)), rng.integers(0, len(spec.times)))
+        r, v = O.sample(f, spec.times[s], spec.lon[i], spec.lat[j], spec.depth[k])
+        assert r == 0
+        np.testing.assert_allclose(v, spec.data[s, :, k, j, i], rtol=0, atol=1e-14)
+
+
+def test_time_periodic_field():
+    lon = np.arange(0.0, 360.0, 10.0)
+    lat = np.linspace(-60.0, 60.0, 5)
+    times = np.array([0.0, 1.0, 2.0]) * DAY
+    data = np.zeros((3, 2, 1, 5, len(lon)))
+    for s in range(3):
+        data[s] = s + 1.0
+    f = O.Field(lon, lat, np.zeros(1), times, data, 1, True, period=4 * DAY)
+    # between the last snapshot (value 3) and the first again at t0 + period (value 1)
+    r, v = O.sample(f, 3.0 * DAY, 5.0, 0.0)
+    assert r == 0 and abs(v[0] - 2.0) < 1e-15
+    for t in (0.3, 1.7, 2.5, 3.9):
+        a = O.sample(f, t * DAY, 5.0, 0.0)[1]
+        b = O.sample(f, (t + 4.0) * DAY, 5.0, 0.0)[1]
+        c = O.sample(f, (t - 8.0) * DAY, 5.0, 0.0)[1]
+        np.testing.assert_allclose(a, b, atol=1e-12)
+        np.testing.assert_allclose(a, c, atol=1e-12)
+    # non-periodic field refuses times outside its range
+    g = O.Field(lon, lat, np.zeros(1), times, data, 1, True)
+    assert O.sample(g, 2.5 * DAY, 5.0, 0.0)[0] == -1
+
+
+# --------------------------------------------------------------------------
+# RK4 / Euler against closed forms (Sect. 4.2.1, 4.2.2, 4.2.3).
+# --------------------------------------------------------------------------
+
+def _rk4_matrix(Z):
+    I = np.eye(2)
+    return I + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+
+
+def test_solid_body_rotation_rk4_closed_form():
+    spec = synth.solid_body_rotation()
+    f = _field(spec)
+    st = _state([0.0] * 4, [1e3, 2e3, 3e3, 4e3])
+    h = 300.0
+    n = _run(f, O.Kernel(O.RK4), st, h, DAY)
+    assert n == 4 * 288 and (st["status"] == 0).all()
+    w = 2 * np.pi / DAY
+    A = np.array([[0.0, -w], [w, 0.0]])
+    M = np.linalg.matrix_power(_rk4_matrix(h * A), 288)
+    ref = M @ np.stack([np.zeros(4), [1e3, 2e3, 3e3, 4e3]])
+    np.testing.assert_allclose(st["lon"], ref[0], rtol=0, atol=1e-8)
+    np.testing.assert_allclose(st["lat"], ref[1], rtol=0, atol=1e-8)
+    # the paper reports < 3 mm after 24 h on this case
+    assert np.max(np.hypot(st["lon"] - 0.0, st["lat"] - [1e3, 2e3, 3e3, 4e3])) < 3e-3
+    assert (st["time"] == DAY).all() and (st["step"] == 288).all()
+
+
+def test_solid_body_rotation_euler_closed_form():
+    spec = synth.solid_body_rotation()
+    f = _field(spec)
+    st = _state([0.0, 500.0], [1e3, -2e3])
+    h = 60.0
+    _run(f, O.Kernel(O.EULER), st, h, 100 * h)
+    w = 2 * np.pi / DAY
+    M = np.linalg.matrix_power(np.eye(2) + h * np.array([[0.0, -w], [w, 0.0]]), 100)
+    ref = M @ np.stack([[0.0, 500.0], [1e3, -2e3]])
+    np.testing.assert_allclose(st["lon"], ref[0], atol=1e-8)
+    np.testing.assert_allclose(st["lat"], ref[1], atol=1e-8)
+
+
+def test_oscillating_flow_is_trapezoid_of_snapshots():
+    """With dt equal to the 5-min snapshot spacing the velocity is linear in
+    time within each step, so RK4 (Simpson) integrates it exactly: the path
+    is the trapezoid sum of the snapshot values."""
+    A, dt = 0.1, 300.0
+    spec = synth.oscillating_flow(A=A, dt_snap=dt)
+    f = _field(spec)
+    x0 = np.linspace(-5e3, 5e3, 20)
+    st = _state(x0, np.zeros(20))
+    u_snap = spec.data[:, 0, 0, 0, 0]
+    w = 2 * np.pi / DAY
+    worst_x = worst_y = 0.0
+    for k in range(1, 33):               # every 3 hours for 4 days
+        t_out = k * 3 * 3600.0
+        _run(f, O.Kernel(O.RK4), st, dt, t_out)
+        m = int(round(t_out / dt))
+        disc = x0 + dt * np.sum((u_snap[:m] + u_snap[1:m + 1]) / 2)
+        np.testing.assert_allclose(st["lon"], disc, rtol=0, atol=1e-9)
+        np.testing.assert_allclose(st["lat"], A * t_out, rtol=0, atol=1e-9)
+        worst_x = max(worst_x, np.max(np.abs(st["lon"] - (x0 + A / w * np.sin(w * t_out)))))
+        worst_y = max(worst_y, np.max(np.abs(st["lat"] - A * t_out)))
+    # the paper reports 6 cm zonal and 4 mm meridional errors after 4 days
+    assert worst_x < 0.06 and worst_y < 0.004
+
+
+def test_zonal_flow_on_sphere():
+    """Uniform 1 m/s eastward flow: lon(t) = lon0 + t / (D cos lat0), lat fixed."""
+    spec = synth.zonal_flow_sphere()
+    f = _field(spec)
+    lat0 = np.arange(-45.0, 45.1, 3.0)
+    st = _state(np.zeros(31), lat0)
+    T = 57 * DAY
+    _run(f, O.Kernel(O.RK4), st, 300.0, T)
+    D = 1852.0 * 60.0
+    ref = np.mod(T / (D * np.cos(np.deg2rad(lat0))), 360.0)
+    np.testing.assert_allclose(st["lon"], ref, rtol=0, atol=1e-8)
+    np.testing.assert_array_equal(st["lat"], lat0)
+    # "almost 45 degrees" at the equator after 57 days at 1 m/s
+    eq = st["lon"][15]
+    assert 44.0 < eq < 45.0
+
+
+def test_decaying_eddy_converges_to_closed_form():
+    errs = []
+    for dt in (600.0, 300.0, 150.0):
+        spec = synth.decaying_eddy(dt_snap=dt)
+        f = _field(spec)
+        x0 = np.array([1e3, -3e3, 5e3])
+        y0 = np.array([2e3, 4e3, -1e3])
+        st = _state(x0, y0)
+        T = 4 * DAY
+        _run(f, O.Kernel(O.RK4), st, dt, T)
+        xr, yr = synth.eddy_trajectory(x0, y0, T)
+        errs.append(np.max(np.hypot(st["lon"] - xr, st["lat"] - yr)))
+    # second order in the snapshot spacing (linear time interpolation)
+    assert errs[1] < errs[0] / 3.0 and errs[2] < errs[1] / 3.0
+    # the paper's damped-oscillation case reports < 5 cm after 4 days at 5 min
+    assert errs[1] < 0.05
+
+
+def test_stommel_gyre_psi_drift_falls_with_resolution():
+    rng = np.random.default_rng(1)
+    L = 1e6
+    x0 = rng.uniform(0.05 * L, 0.95 * L, 100)
+    y0 = rng.uniform(0.05 * L, 0.95 * L, 100)
+    drift = []
+    for n in (101, 201, 401):
+        f = _field(synth.stommel_gyre(n=n))
+        st = _state(x0, y0)
+        _run(f, O.Kernel(O.RK4), st, 3600.0, 30 * DAY)
+        assert (st["status"] == 0).all()
+        d = np.abs(synth.stommel_psi(st["lon"], st["lat"]) - synth.stommel_psi(x0, y0))
+        drift.append(np.max(d))
+    assert drift[1] < drift[0] / 2 and drift[2] < drift[1] / 2
+    assert drift[1] < 0.01 * 1e5
+
+
+def test_peninsula_psi_conservation():
+    y0 = np.linspace(26e3, 52e3, 20)
+    x0 = np.full(20, 1000.0)
+    drift = []
+    for nx, ny in ((101, 51), (201, 101)):
+        f = _field(synth.peninsula(nx=nx, ny=ny))
+        st = _state(x0, y0)
+        _run(f, O.Kernel(O.RK4), st, 300.0, 20 * 3600.0)
+        ok = st["status"] == 0
+        assert ok.sum() >= 15
+        d = np.abs(synth.peninsula_psi(st["lon"], st["lat"]) - synth.peninsula_psi(x0, y0))[ok]
+        drift.append(np.max(d))
+    assert drift[1] < drift[0] / 2
+    assert drift[0] < 20.0    # m^2/s, against |psi| up to 5e4 m^2/s
+
+
+# --------------------------------------------------------------------------
+# Behaviours, boundary and time handling.
+# --------------------------------------------------------------------------
+
+def test_brownian_variance_2kt():
+    """Sect. 4.2.7: K_h = 100, 1e5 particles, 1 day, dt 5 min; per-axis
+    variance 2 K t (sigma = 4.16 km), zero mean, Gaussian shape."""
+    from scipy import stats
+    f = _field(synth.zero_field())
+    N = 100_000
+    st = _state(np.zeros(N), np.zeros(N))
+    K, T = 100.0, DAY
+    _run(f, O.Kernel(O.RK4, O.BROWNIAN, kh=K, seed=7), st, 300.0, T)
+    assert (st["status"] == 0).all()
+    var = 2 * K * T
+    assert abs(np.sqrt(var) - 4157.0) < 1.0
+    tol = 4 * np.sqrt(2.0 / N)
+    for a in (st["lon"], st["lat"]):
+        assert abs(np.var(a) / var - 1.0) < tol
+        assert abs(np.mean(a)) < 4 * np.sqrt(var / N)
+        assert stats.kstest(a / np.sqrt(var), "norm").pvalue > 1e-4
+    assert abs(np.corrcoef(st["lon"], st["lat"])[0, 1]) < 4 / np.sqrt(N)
+
+
+def test_brownian_on_sphere_uses_metres_per_degree():
+    spec = synth.zonal_flow_sphere(u=0.0)
+    f = _field(spec)
+    N = 20000
+    lat0 = 60.0
+    st = _state(np.full(N, 100.0), np.full(N, lat0))
+    K, dt = 10.0, 3600.0
+    _run(f, O.Kernel(O.EULER, O.BROWNIAN, kh=K, seed=3), st, dt, dt)
+    D = 1852.0 * 60.0
+    sig = np.sqrt(2 * K * dt)
+    tol = 4 * np.sqrt(2.0 / N)
+    assert abs(np.std(st["lat"] - lat0) * D / sig - 1) < tol
+    assert abs(np.std(st["lon"] - 100.0) * D * np.cos(np.deg2rad(lat0)) / sig - 1) < 3 * tol
+
+
+def test_sinking_is_linear():
+    rng = np.random.default_rng(3)
+    spec, _ = synth.linear_field(rng, nz=6, nt=1)
+    spec.data = np.zeros_like(spec.data)
+    f = _field(spec)
+    d0 = np.array([10.0, 50.0])
+    st = _state([0.0, 1e3], [2e3, 3e3], d0)
+    w, dt = 2e-3, 600.0
+    _run(f, O.Kernel(O.RK4, O.SINK, w_sink=w), st, dt, 100 * dt)
+    np.testing.assert_allclose(st["depth"], d0 + 100 * w * dt, rtol=0, atol=1e-9)
+    # then it sinks through the bottom level and is deleted there
+    _run(f, O.Kernel(O.RK4, O.SINK, w_sink=w), st, dt, 10000 * dt)
+    assert (st["status"] == O.OOB_DEPTH).all()
+    assert (st["depth"] <= spec.depth[-1]).all()
+    assert (st["depth"] + w * dt > spec.depth[-1]).all()
+
+
+def test_out_of_bounds_deletes_and_keeps_last_valid_state():
+    spec = synth.uniform_flow(u=0.0, v=0.5, half_width=1e4)
+    f = _field(spec)
+    y0 = np.array([0.0, 5000.0, 9000.0])
+    st = _state(np.zeros(3), y0)
+    dt = 1000.0
+    _run(f, O.Kernel(O.RK4), st, dt, 100 * dt)
+    assert (st["status"] == O.OOB_HORIZ).all()
+    # the step that would leave y <= 1e4 is not applied
+    nmax = np.floor((1e4 - y0) / (0.5 * dt))
+    np.testing.assert_allclose(st["lat"], y0 + nmax * 0.5 * dt, atol=1e-9)
+    np.testing.assert_array_equal(st["time"], nmax * dt)
+    np.testing.assert_array_equal(st["step"], nmax.astype(np.uint32))
+
+
+def test_euler_uniform_flow_and_time_clamp():
+    spec = synth.uniform_flow(u=0.3, v=-0.2)
+    f = _field(spec)
+    st = _state([0.0], [0.0])
+    _run(f, O.Kernel(O.EULER), st, 700.0, 1e9, 10000.0)
+    assert st["time"][0] == 10000.0          # 14 steps of 700 s and one of 200 s
+    assert st["step"][0] == 15
+    np.testing.assert_allclose([st["lon"][0], st["lat"][0]], [3000.0, -2000.0], atol=1e-9)
+
+
+def test_backward_in_time_returns_to_start():
+    f = _field(synth.solid_body_rotation())
+    y0 = np.array([1e3, 2.5e3, 4e3])
+    st = _state(np.zeros(3), y0)
+    _run(f, O.Kernel(O.RK4), st, 300.0, DAY / 2)
+    _run(f, O.Kernel(O.RK4), st, -300.0, 0.0)
+    np.testing.assert_allclose(st["lon"], 0.0, atol=1e-6)
+    np.testing.assert_allclose(st["lat"], y0, atol=1e-6)
+    assert (st["time"] == 0.0).all()
+
+
+def test_nan_velocity_deletes():
+    spec = synth.uniform_flow(u=0.1, v=0.1, n=5, half_width=1e4)
+    spec.data[0, 0, 0, 2, 2] = np.nan
+    f = _field(spec)
+    st = _state([-4000.0, 100.0], [-4000.0, 100.0])
+    _run(f, O.Kernel(O.RK4), st, 100.0, 1000.0)
+    assert st["status"][1] == O.NAN and st["step"][1] == 0
+    assert st["status"][0] == O.NAN or st["status"][0] == O.ALIVE
+
+
+# --------------------------------------------------------------------------
+# Random numbers and reduced-precision storage.
+# --------------------------------------------------------------------------
+
+def test_philox_structure_and_statistics():
+    from scipy import stats
+    # each round is a bijection of the counter for a fixed key
+    rng = np.random.default_rng(0)
+    outs = set()
+    for _ in range(2000):
+        c = rng.integers(0, 2 ** 32, 4, dtype=np.uint64).astype(np.uint32)
+        outs.add(tuple(O.philox4x32_10(c, [1, 2])))
+    assert len(outs) == 2000
+    # uniform bytes: chi-square over 256 bins of 4*2^14 words
+    words = np.concatenate([O.philox4x32_10([i, 0, 0, 0], [123, 456]) for i in range(1 << 14)])
+    for shift in (0, 8, 16, 24):
+        counts = np.bincount((words >> shift) & 0xFF, minlength=256)
+        assert stats.chisquare(counts).pvalue > 1e-4
+    # changing one counter bit flips about half of the output bits
+    base = O.philox4x32_10([7, 0, 0, 0], [9, 9])
+    flips = []
+    for k in range(32):
+        other = O.philox4x32_10([7 ^ (1 << k), 0, 0, 0], [9, 9])
+        flips += [bin(int(a) ^ int(b)).count("1") for a, b in zip(base, other)]
+    assert 10 < np.mean(flips) < 22
+    # normal pairs: N(0, 1) moments and independence of the two variates
+    z = np.array([O.normal_pair(5, i, 3) for i in range(40000)])
+    assert abs(z.mean()) < 0.03 and abs(z.var() - 1) < 0.03
+    assert abs(np.corrcoef(z[:, 0], z[:, 1])[0, 1]) < 0.03
+    assert O.normal_pair(5, 1, 3) != O.normal_pair(5, 1, 4) != O.normal_pair(6, 1, 3)
+
+
+def test_f16_quantisation_matches_numpy_round_to_nearest_even():
+    rng = np.random.default_rng(4)
+    v = np.concatenate([
+        rng.normal(size=20000).astype(np.float32) * 100,
+        np.float32(2.0) ** rng.integers(-30, 17, 20000).astype(np.float32) *
+        rng.uniform(1, 2, 20000).astype(np.float32),
+        np.array([0.0, -0.0, 65504.0, 65519.0, 65520.0, 1e-8, 2.0 ** -25, 2.0 ** -24,
+                  3 * 2.0 ** -26, 5.960464477539063e-08, 6.103515625e-05], dtype=np.float32),
+    ]).astype(np.float32)
+    import ctypes
+    lib = O.lib()
+    lib.or_f32_to_f16.argtypes = [ctypes.c_float]
+    lib.or_f32_to_f16.restype = ctypes.c_uint16
+    mine = np.array([lib.or_f32_to_f16(float(x)) for x in v], dtype=np.uint16)
+    with np.errstate(over="ignore"):
+        ref = v.astype(np.float16).view(np.uint16)
+    np.testing.assert_array_equal(mine, ref)
+
+
+def test_bf16_quantisation_matches_torch():
+    torch = pytest.importorskip("torch")
+    import ctypes
+    rng = np.random.default_rng(6)
+    v = np.concatenate([rng.normal(size=20000) * 10, rng.uniform(-1e-3, 1e-3, 20000),
+                        [0.0, 1.0, 1.00390625, 1.005859375, -3.0e38]]).astype(np.float32)
+    lib = O.lib()
+    lib.or_f32_to_bf16.argtypes = [ctypes.c_float]
+    lib.or_f32_to_bf16.restype = ctypes.c_uint16
+    mine = np.array([lib.or_f32_to_bf16(float(x)) for x in v], dtype=np.uint16)
+    ref = torch.from_numpy(v).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    np.testing.assert_array_equal(mine, ref)
+
+
+def test_quantise_scale_and_dequantise():
+    rng = np.random.default_rng(8)
+    v = (rng.normal(size=5000) * 0.3).astype(np.float32)
+    for kind, rel in ((0, 2.0 ** -11), (1, 2.0 ** -8)):
+        q, s = O.quantise(v, kind)
+        assert s == np.float32(np.max(np.abs(v)) / np.float32(32752.0))
+        back = O.dequantise(q, kind, s)
+        if kind == 0:
+            np.testing.assert_array_equal(
+                back, (q.view(np.float16).astype(np.float32) * s).astype(np.float64))
+        err = np.abs(back - v)
+        assert np.all(err <= rel * np.abs(v) * 1.001 + 2.0 ** -24 * s * 1.001)
