@@ -111,7 +111,7 @@ int or_locate_lon(const double *x, int n, int periodic, double p,
         *i1 = (n == 1) ? *i0 : *i0 + 1;
         return 0;
     }
-    if (!(p == p)) return 1;
+    if (!isfinite(p)) return 1;
     double q = or_wrap_lon(p, x[0]);
     if (q >= x[n - 1]) {
         *i0 = n - 1;
@@ -292,6 +292,7 @@ void or_normal_pair(uint64_t seed, uint64_t id, uint32_t step, double *n1, doubl
 static int out_of_domain(const or_fieldset *fs, double lon, double lat, double depth)
 {
     if (!fs->periodic_lon && !(lon >= fs->lon[0] && lon <= fs->lon[fs->nx - 1])) return OR_OOB_HORIZ;
+    if (fs->periodic_lon && !(lon == lon)) return OR_OOB_HORIZ;   /* no longer a number */
     if (!(lat >= fs->lat[0] && lat <= fs->lat[fs->ny - 1])) return OR_OOB_HORIZ;
     if (fs->nz > 1 && !(depth >= fs->depth[0] && depth <= fs->depth[fs->nz - 1])) return OR_OOB_DEPTH;
     return OR_ALIVE;
