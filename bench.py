@@ -1,0 +1,387 @@
+"""Benchmark: RK4 particle-steps/s of the 3-D FP32 advection step on a global
+1/4-degree grid (1440 x 720 x 50 levels, 30 daily snapshots of U, V, W, two
+bracketing snapshots sampled per stage, periodic zonal boundary, deletion out
+of the depth/latitude range), 10 million particles in the upper 1000 m, dt 30
+minutes for 30 days (1440 steps).
+
+One bench step = one full execute of that workload from the seeded start
+state.  `value` times the steps with the field and particles resident in HBM;
+`e2e` runs the same workload through the C ABI from host buffers (snapshots
+streamed host-to-device during the run, particles uploaded and results read
+back inside the timed region).  `--impl reference` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+
+Launch: python bench.py [--steps K] [--warmup W]   (N > 1 under torchrun)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DAY = 86400.0
+ALGO_BYTES_PER_STEP = 810.0      # 3-D FP32 RK4: 768 B of field gathers + 42 B of state
+ALGO_FLOPS_PER_STEP = 450.0
+METRIC = "RK4 particle-steps/s on 1 GB300, chosen form vs plain FP32 at ≤1e-3-cell error"
+UNIT = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--particles", type=int, default=10_000_000)
+    ap.add_argument("--days", type=float, default=30.0)
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--resort-steps", type=int, default=0)
+    ap.add_argument("--chunk-steps", type=int, default=48)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("advect_plain.cuh", "advect_f32.cu", "pg_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1707_05163_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch():
+    """DRAM bytes per launch of the advection kernel from a committed ncu
+    capture, if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "advect_f32_3d_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        if d.get("kernel_hash") == kernel_hash():
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_field_host_bases(gf):
+    return [gf.base2d(s) for s in range(len(gf.times))]
+
+
+def oracle_baseline(gf, host_field, lon, lat, dep, days, seconds_budget):
+    """The FP64 oracle on a bounded sample of the workload, on this host's cores."""
+    import oracle as O
+    cores = len(os.sched_getaffinity(0))
+    f = O.Field(gf.lon, gf.lat, gf.depth, gf.times, host_field, 1, True, gf.period)
+    k = O.Kernel(O.RK4)
+
+    def run(n, steps_days):
+        st = [np.array(lon[:n], np.float64), np.array(lat[:n], np.float64),
+              np.array(dep[:n], np.float64), np.zeros(n), np.arange(n, dtype=np.uint64),
+              np.zeros(n, np.uint32), np.zeros(n, np.uint8)]
+        t0 = time.perf_counter()
+        done = O.run(f, k, *st, 1800.0, steps_days * DAY, steps_days * DAY, nthreads=cores)
+        return done, time.perf_counter() - t0
+
+    n0 = 32 * cores
+    done, dt = run(n0, days)
+    n = int(min(len(lon), max(n0, n0 * seconds_budget / max(dt, 1e-3))))
+    done, dt = run(n, days)
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n} of the workload's particles, full {days:g}-day horizon, "
+                      f"{done} particle-steps in {dt:.1f} s"}, done, dt
+
+
+def build_fieldset_device(pg, gf, torch, dev, bases, host_field=None):
+    """All snapshots resident: each slab built on the device (float32 of the
+    FP64 product base x profile, the same values the host generator makes)."""
+    fs = pg.FieldSet(gf.lon, gf.lat, gf.depth, mesh="spherical", periodic_lon=True,
+                     nfields=gf.nfields, storage="f32")
+    fs.set_times(gf.times, gf.period)
+    prof = torch.from_numpy(gf.profiles()).to(dev)
+    for s, b in enumerate(bases):
+        base = torch.from_numpy(b).to(dev)
+        slab = (base[:, None, :, :] * prof[:, :, None, None]).to(torch.float32)
+        fs.load_snapshot(s, slab)
+        if host_field is not None:
+            host_field[s].copy_(slab)
+        del slab, base
+    torch.cuda.synchronize()
+    return fs
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    import torch
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import paper_1707_05163_gb300 as pg
+    import synth
+    pg.load()
+
+    gf = synth.GlobalField(res_deg=0.25, nz=50, nt=30, seed=2)
+    bases = make_field_host_bases(gf)
+    want_host = (not args.no_e2e) or (rank == 0 and world == 1 and not args.no_cpu)
+    host_field = None
+    if want_host:
+        try:
+            host_field = torch.empty((len(gf.times), gf.nfields, gf.nz, gf.ny, gf.nx),
+                                     dtype=torch.float32, pin_memory=True)
+        except Exception:
+            host_field = None
+    fs = build_fieldset_device(pg, gf, torch, dev, bases, host_field)
+
+    n = args.particles
+    lon, lat, dep = synth.uniform_particles(n, 2 + rank, (0.0, 360.0), (-80.0, 80.0),
+                                            (5.0, 1000.0), dtype=np.float32)
+    dlon = torch.from_numpy(lon).to(dev)
+    dlat = torch.from_numpy(lat).to(dev)
+    ddep = torch.from_numpy(dep).to(dev)
+    kern = pg.Kernel("rk4")
+    runtime = args.days * DAY
+    lib = pg.load()
+    import ctypes as C
+
+    def one_step(timing=False):
+        ps = pg.ParticleSet(fs, dlon, dlat, ddep, pos="f32", seed=0)
+        ps.set_tune(args.block, args.resort_steps, args.chunk_steps)
+        if timing:
+            lib.pg_pset_kernel_timing(ps.h, 1, None, None)
+        steps = ps.execute(kern, runtime, 1800.0)
+        ms, launches = C.c_double(), C.c_int64()
+        if timing:
+            lib.pg_pset_kernel_timing(ps.h, -1, C.byref(ms), C.byref(launches))
+        ps.destroy()
+        return steps, ms.value, launches.value
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    c0 = C.c_int64()
+    lib.pg_launch_count(C.byref(c0))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    total_steps, kern_ms, kern_launches = 0, 0.0, 0
+    for _ in range(args.steps):
+        s, ms, ln = one_step(timing=True)
+        total_steps += s
+        kern_ms += ms
+        kern_launches += ln
+    ev1.record()
+    torch.cuda.synchronize()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    c1 = C.c_int64()
+    lib.pg_launch_count(C.byref(c1))
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms, float(total_steps)], device=dev, dtype=torch.float64)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        elapsed_ms, total_all = float(mx[0]), float(sm[1])
+    else:
+        total_all = float(total_steps)
+    value = total_all / (elapsed_ms / 1e3)
+
+    # end-to-end through the C ABI from host buffers
+    e2e = None
+    if not args.no_e2e and host_field is not None:
+        e2e = e2e_leg(pg, gf, torch, host_field, lon, lat, dep, kern, runtime, args)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu and host_field is not None:
+        cpu, _, _ = oracle_baseline(gf, host_field.numpy(), lon, lat, dep, args.days,
+                                    args.cpu_seconds)
+
+    peak, peak_kind = measured_peaks()
+    avg_launch_s = (kern_ms / 1e3) / max(kern_launches, 1)
+    steps_per_launch = total_steps / max(kern_launches, 1)
+    achieved = ALGO_BYTES_PER_STEP * steps_per_launch / avg_launch_s / 1e9
+    traffic = traffic_per_launch()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded k^-3 random streamfunction field, uniform particles)",
+        "config": {"workload": "3-D FP32 RK4, global 1/4 deg 1440x720x50, 30 daily snapshots "
+                               "(periodic), 10M particles upper 1000 m, dt 30 min, 30 days",
+                   "particles_per_gpu": n, "days": args.days, "dt_s": 1800.0,
+                   "block": args.block, "resort_steps": args.resort_steps,
+                   "chunk_steps": args.chunk_steps, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (24.9 GB field, 10M-particle state)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_kind,
+                     "kernel": "advect_plain_kernel<float,float,3,true>",
+                     "algorithmic_bytes_per_particle_step": ALGO_BYTES_PER_STEP,
+                     "avg_launch_ms": avg_launch_s * 1e3, "launches": kern_launches},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(c1.value - c0.value),
+        "clocks": clk,
+        "particle_steps": total_all,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def e2e_leg(pg, gf, torch, host_field, lon, lat, dep, kern, runtime, args):
+    """Same workload from host memory: snapshots streamed H2D inside execute,
+    particles uploaded and final state read back, all inside the timed region."""
+    import ctypes as C
+    n = len(lon)
+    fs = pg.FieldSet(gf.lon, gf.lat, gf.depth, mesh="spherical", periodic_lon=True,
+                     nfields=gf.nfields, storage="f32")
+    fs.set_times(gf.times, gf.period)
+    fs.stream([host_field[s] for s in range(len(gf.times))])
+    hl = torch.from_numpy(lon).pin_memory()
+    ha = torch.from_numpy(lat).pin_memory()
+    hd = torch.from_numpy(dep).pin_memory()
+    out = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in ("lon", "lat", "depth")}
+    ost = torch.empty(n, dtype=torch.uint8).pin_memory()
+    lib = pg.load()
+    best = None
+    h2d_field = 0
+    for rep in range(2):
+        lib.pg_fieldset_stats(fs.h, 1, None, None)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ps = pg.ParticleSet(fs, hl, ha, hd, pos="f32", seed=0)
+        ps.set_tune(args.block, args.resort_steps, args.chunk_steps)
+        steps = ps.execute(kern, runtime, 1800.0)
+        ps.get_into(lon=out["lon"], lat=out["lat"], depth=out["depth"], status=ost)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ps.destroy()
+        ub = C.c_int64()
+        lib.pg_fieldset_stats(fs.h, 1, None, C.byref(ub))
+        if best is None or dt < best[0]:
+            best = (dt, steps)
+            h2d_field = ub.value
+    h2d = h2d_field + n * 3 * 4          # snapshot uploads + float32 positions
+    d2h = n * (3 * 8 + 1)
+    fs.destroy()
+    return {"value": best[1] / best[0], "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "seconds": best[0]}
+
+
+def reference_arm(args, rank, world):
+    """The FP64 CPU oracle as the reference arm, on a bounded sample per step."""
+    if rank != 0:
+        return
+    import synth
+    gf = synth.GlobalField(res_deg=0.25, nz=50, nt=30, seed=2)
+    field = np.empty((len(gf.times), gf.nfields, gf.nz, gf.ny, gf.nx), dtype=np.float32)
+    for s in range(len(gf.times)):
+        field[s] = gf.slab(s)
+    lon, lat, dep = synth.uniform_particles(args.particles, 2, (0.0, 360.0), (-80.0, 80.0),
+                                            (5.0, 1000.0), dtype=np.float32)
+    budget = max(2.0, 120.0 / max(args.steps + args.warmup, 1))
+    cpu, done, dt = None, 0, 0.0
+    for i in range(args.warmup + args.steps):
+        c, d, t = oracle_baseline(gf, field, lon, lat, dep, args.days, budget)
+        if i >= args.warmup:
+            done += d
+            dt += t
+            cpu = c
+    value = done / dt
+    cpu["value"] = value
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "3-D RK4, global 1/4 deg 1440x720x50, 30 daily "
+                                                    "snapshots, dt 30 min, 30 days (oracle sample)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,279 @@
+/*
+ * parcels_gb.h -- C ABI of the GB300 particle-advection library.
+ *
+ * The library advects many independent virtual particles through gridded
+ * velocity fields (Lange & van Sebille, "Parcels v0.9", arXiv 1707.05163):
+ * each step integrates Eq. 1 with RK4 (default) or Euler-forward (Sect.
+ * 2.1.1), sampling U, V[, W] by bi/trilinear interpolation in space and linear
+ * interpolation in time on a rectilinear grid (Sect. 2.3, 2.4), then applies
+ * composable behaviours -- Brownian motion with uniform K_h (Sect. 2.1.2,
+ * 4.2.7) and constant sinking (the behaviour term of Eq. 1) -- a periodic
+ * zonal boundary and deletion of particles that leave the domain (the
+ * out-of-bounds recovery of Sect. 2.1.2 and 3).  The objects follow the
+ * paper's FieldSet / ParticleSet / Kernel / execute statement of the problem
+ * (Sect. 2.1, 2.2, 3; Fig. 2).
+ *
+ * Conventions for every call:
+ *   - Return value: PG_OK (0) or a negative PG_ERR_* code.  On error the
+ *     objects are left as they were before the call, and pg_last_error()
+ *     returns a message for the calling thread.  No call throws or aborts.
+ *   - Pointers named "host or device" may point to host memory (pageable or
+ *     pinned) or to device memory of the current CUDA device; the library
+ *     copies from them during the call (unified addressing).  The caller keeps
+ *     ownership of everything it passes in; the library owns what it creates
+ *     and frees it in the matching pg_*_destroy.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All
+ *     device work of a call is ordered on it; calls return after the work
+ *     they launched has completed unless stated otherwise.
+ *   - Units: flat mesh positions in metres; spherical mesh lon/lat in degrees;
+ *     depth in metres, positive downward; velocities in m/s (W positive
+ *     downward); times and dt in seconds.
+ */
+#ifndef PARCELS_GB_H
+#define PARCELS_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int pg_status;
+
+/* Symbols of this header are exported from the shared library. */
+#if defined(__GNUC__)
+#define PG_API __attribute__((visibility("default")))
+#else
+#define PG_API
+#endif
+
+/* Error codes. */
+#define PG_OK 0
+#define PG_ERR_ARG (-1)         /* invalid argument; nothing changed            */
+#define PG_ERR_CUDA (-2)        /* a CUDA call failed                           */
+#define PG_ERR_STATE (-3)       /* call not valid in the object's current state */
+#define PG_ERR_TIME (-4)        /* time span outside the field's time range     */
+#define PG_ERR_CALLBACK (-5)    /* a user callback returned non-zero            */
+#define PG_ERR_TIMEOUT (-6)     /* a bounded device wait gave up                */
+#define PG_ERR_NOMEM (-7)       /* device or host allocation failed             */
+#define PG_ERR_UNSUPPORTED (-8) /* combination of options not implemented       */
+#define PG_ERR_DEVICE (-9)      /* a kernel recorded an internal check failure  */
+
+/* Mesh (Sect. 4.2.2): flat (metres) or spherical (degrees, converted with
+ * 1852*60 metres per degree of latitude, and per degree of longitude times
+ * the cosine of latitude). */
+#define PG_FLAT 0
+#define PG_SPHERICAL 1
+
+/* Field storage in device memory.  F16S/BF16S store binary16/bfloat16 codes
+ * with one FP32 scale per (field, snapshot): scale = max|v| / 32752,
+ * code = round-to-nearest-even(v / scale), value = code * scale. */
+#define PG_F64 0
+#define PG_F32 1
+#define PG_F16S 2
+#define PG_BF16S 3
+
+/* Particle position representation.  F64/F32: lon, lat, depth.  CELL: an
+ * int32 cell index per axis plus an FP32 offset in [0, 1) inside the cell
+ * (requires uniformly spaced axes). */
+#define PG_POS_F64 0
+#define PG_POS_F32 1
+#define PG_POS_CELL 2
+
+/* Time-stepping scheme (Sect. 2.1.1). */
+#define PG_EULER 0
+#define PG_RK4 1
+
+/* Behaviour bits, applied after advection in this order. */
+#define PG_BROWNIAN 1u
+#define PG_SINK 2u
+
+/* Particle status (one byte per particle).  Any non-zero status means the
+ * particle was deleted; its position and time are those before the step
+ * that would have taken it out of the domain. */
+#define PG_ALIVE 0
+#define PG_OOB_HORIZ 1 /* a stage or final position left the lon/lat range */
+#define PG_OOB_DEPTH 2 /* a stage or final position left the depth range   */
+#define PG_NAN 3       /* a sampled velocity was NaN                        */
+
+typedef struct pg_fieldset pg_fieldset;
+typedef struct pg_pset pg_pset;
+typedef struct pg_kernel pg_kernel;
+
+/* Rectilinear grid (Sect. 2.4): each axis depends on one coordinate only.
+ * lon[nx], lat[ny], depth[nz] strictly increasing, host memory, copied.
+ * nz == 1 makes a two-dimensional field (depth ignored by the sampling). */
+typedef struct {
+    int nx, ny, nz;
+    const double *lon, *lat, *depth;
+} pg_grid;
+
+/* Tuning of the time loop.  Zero fields take defaults. */
+typedef struct {
+    int block;          /* threads per block of the advection kernel (default 256)  */
+    int resort_steps;   /* Morton re-sort every this many steps (0: never)           */
+    int chunk_steps;    /* at most this many steps per kernel launch (default 64)    */
+} pg_tune;
+
+/* Snapshot source for streamed fields (the counterpart of advancing the
+ * resident time slices, Sect. 3).  Fill `dst` (host, pinned, `bytes` long)
+ * with snapshot `s` laid out [nfields][nz][ny][nx] in the source dtype given
+ * to pg_fieldset_stream.  Return 0 on success; non-zero aborts the execute
+ * with PG_ERR_CALLBACK. */
+typedef int (*pg_snapshot_cb)(void *user, int s, void *dst, size_t bytes);
+
+/* Output hook, called at every output time (the ParticleFile of Sect. 3).
+ * Arrays are host memory valid during the call only, n entries in the
+ * library's internal order (use `id` to match particles).  Non-zero return
+ * aborts the execute with PG_ERR_CALLBACK. */
+typedef int (*pg_output_cb)(void *user, double time, int64_t n, const uint64_t *id,
+                            const double *lon, const double *lat, const double *depth,
+                            const uint8_t *status);
+
+/* ---------------------------------------------------------------- errors */
+
+/* Message describing the last error on the calling thread ("" if none). */
+PG_API const char *pg_last_error(void);
+
+/* Library version string. */
+PG_API const char *pg_version(void);
+
+/* -------------------------------------------------------------- fieldset */
+
+/* Create a field set (the FieldSet of Sect. 2.4) on the current CUDA device.
+ * nfields: 2 (U, V) or 3 (U, V, W; needs nz > 1).  periodic_lon requires a
+ * spherical mesh whose lon axis spans less than 360 degrees; the wrap cell
+ * joins the last node to the first.  storage: PG_F64, PG_F32, PG_F16S,
+ * PG_BF16S.  The field holds no data until snapshots are given. */
+PG_API pg_status pg_fieldset_create(const pg_grid *grid, int mesh, int periodic_lon, int nfields,
+                             int storage, pg_fieldset **out);
+
+/* Snapshot times (strictly increasing, host memory, nt >= 1; nt == 1 is a
+ * steady field).  period > 0 makes the field repeat with that period: after
+ * the last snapshot it interpolates towards the first at times[0] + period.
+ * Must be called before any snapshot is given; resets existing data. */
+PG_API pg_status pg_fieldset_set_times(pg_fieldset *fs, int nt, const double *times, double period);
+
+/* Give snapshot s (host or device memory, [nfields][nz][ny][nx], lon
+ * fastest, src_dtype PG_F64 or PG_F32).  The library converts it to its
+ * storage format in device memory it owns (all snapshots resident). */
+PG_API pg_status pg_fieldset_load_snapshot(pg_fieldset *fs, int s, const void *data, int src_dtype,
+                                    void *stream);
+
+/* Stream snapshots instead of keeping them all resident: the library keeps
+ * four device slots and, during pg_execute, uploads the next snapshot on its
+ * own side stream while the current ones are in use.  Source: either `ptrs`
+ * (nt host or device pointers, each valid for the lifetime of the field
+ * set), or `cb` (called with a pinned host buffer to fill).  Exactly one of
+ * ptrs / cb must be non-NULL. */
+PG_API pg_status pg_fieldset_stream(pg_fieldset *fs, const void *const *ptrs, pg_snapshot_cb cb,
+                             void *user, int src_dtype);
+
+/* Device bytes held by the field set's snapshot storage. */
+PG_API pg_status pg_fieldset_device_bytes(const pg_fieldset *fs, size_t *bytes);
+
+/* FP32 scale of (field f, snapshot s) for F16S/BF16S storage (1.0 otherwise).
+ * Resident storage only. */
+PG_API pg_status pg_fieldset_get_scale(const pg_fieldset *fs, int s, int f, float *scale);
+
+PG_API pg_status pg_fieldset_destroy(pg_fieldset *fs);
+
+/* ---------------------------------------------------------------- kernel */
+
+/* A composed kernel (Sect. 2.1.2): advection scheme followed by behaviours.
+ * kh: Brownian diffusivity in m^2/s (sigma per step sqrt(2 kh |dt|) metres,
+ * normal variates from Philox4x32-10 keyed by the particle set's seed and
+ * counted by (particle id, particle step)); w_sink: sinking speed in m/s
+ * (depth += w_sink * dt). */
+PG_API pg_status pg_kernel_create(int scheme, unsigned behaviours, double kh, double w_sink,
+                           pg_kernel **out);
+PG_API pg_status pg_kernel_destroy(pg_kernel *k);
+
+/* ---------------------------------------------------------- particle set */
+
+/* Create a particle set (the ParticleSet of Sect. 2.1) of n particles on the
+ * field set's grid.  lon, lat, depth, time: n doubles each (host or device);
+ * depth may be NULL for zero, time may be NULL for t0 everywhere (then
+ * `t0` is used).  ids: n uint64 (host or device) or NULL for
+ * id_base + 0..n-1.  pos: PG_POS_F64 / PG_POS_F32 / PG_POS_CELL.  The field
+ * set must outlive the particle set. */
+PG_API pg_status pg_pset_create(pg_fieldset *fs, int64_t n, const double *lon, const double *lat,
+                         const double *depth, const double *time, double t0,
+                         const uint64_t *ids, uint64_t id_base, int pos, uint64_t seed,
+                         pg_pset **out);
+
+/* Append particles between executes (the repeated releases of Sect. 3). */
+PG_API pg_status pg_pset_add(pg_pset *ps, int64_t n, const double *lon, const double *lat,
+                      const double *depth, const double *time, double t0, const uint64_t *ids,
+                      uint64_t id_base);
+
+/* Number of particles (alive and deleted) and of alive particles. */
+PG_API pg_status pg_pset_size(const pg_pset *ps, int64_t *n, int64_t *n_alive);
+
+/* Copy the particle state out (library order).  Any pointer may be NULL.
+ * Host or device destinations of n entries each. */
+PG_API pg_status pg_pset_get(const pg_pset *ps, double *lon, double *lat, double *depth, double *time,
+                      uint64_t *ids, uint32_t *steps, uint8_t *status, void *stream);
+
+/* Tuning (block size, re-sort interval, steps per launch). */
+PG_API pg_status pg_pset_set_tune(pg_pset *ps, const pg_tune *tune);
+
+/* Advance every alive particle (the execute of Sect. 2.2 and 3): from the
+ * particle set's time by `runtime` seconds with steps of dt (dt < 0 runs
+ * backward in time).  Each particle steps while its own time lies before the
+ * end time; the last step is shortened to land on it.  If output_dt > 0 and
+ * out != NULL, `out` is called at every multiple of output_dt after the
+ * start and at the end.  Writes the number of particle-steps taken to
+ * *steps_done if non-NULL. */
+PG_API pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
+                     double output_dt, pg_output_cb out, void *user, void *stream,
+                     int64_t *steps_done);
+
+/* Morton re-sort now: order particles by the Morton code of their cell
+ * indices and move deleted particles behind the alive ones. */
+PG_API pg_status pg_pset_resort(pg_pset *ps, void *stream);
+
+/* FP64 moments of the alive particles' positions (deleted ones excluded):
+ * out[0..6] = count, sum lon, sum lat, sum depth, sum lon^2, sum lat^2,
+ * sum depth^2, accumulated in FP64 in a fixed order (deterministic). */
+PG_API pg_status pg_pset_moments(const pg_pset *ps, double out[7], void *stream);
+
+/* Checkpoint: write / read the complete particle state (positions, times,
+ * ids, step counters, status, seed) to a file.  Restoring gives a set that
+ * continues bit-identically. */
+PG_API pg_status pg_pset_save(const pg_pset *ps, const char *path);
+PG_API pg_status pg_pset_restore(pg_fieldset *fs, const char *path, pg_pset **out);
+
+PG_API pg_status pg_pset_destroy(pg_pset *ps);
+
+/* ------------------------------------------------------- instrumentation */
+
+/* CUDA-event timing of the advection launches of pg_execute, recorded on the
+ * execute's stream around every launch.  Returns the time and number of
+ * launches accumulated since timing was last enabled; enable = 1 turns timing
+ * on and resets the totals, 0 turns it off and resets, -1 only reads. */
+PG_API pg_status pg_pset_kernel_timing(pg_pset *ps, int enable, double *total_ms,
+                                       int64_t *launches);
+
+/* Streaming statistics of a field set: snapshot uploads and the bytes copied
+ * host-to-device for them since the last reset (reset != 0 clears after
+ * reading). */
+PG_API pg_status pg_fieldset_stats(pg_fieldset *fs, int reset, int64_t *uploads,
+                                   int64_t *h2d_bytes);
+
+/* Number of kernel launches the library has made in this process. */
+PG_API pg_status pg_launch_count(int64_t *count);
+
+/* ------------------------------------------------------------ test hooks */
+
+/* Make every later device allocation of the library fail once the library
+ * has allocated `bytes` more than it holds now (negative: no limit).  Used to
+ * test that a failed allocation leaves objects unchanged. */
+PG_API pg_status pg_debug_set_alloc_limit(int64_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PARCELS_GB_H */

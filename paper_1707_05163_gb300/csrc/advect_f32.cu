@@ -1,0 +1,33 @@
+// advect_f32.cu -- FP32 instantiations of the plain advection chunk (FP32
+// positions; FP32, FP16 or BF16 field storage).
+#include "advect_plain.cuh"
+#include "pg_host.h"
+
+namespace pg {
+
+cudaError_t launch_advect_f64(const StepArgs &a, int storage, int block, cudaStream_t st);
+
+template <typename Store>
+static cudaError_t launch_f32(const StepArgs &a, int block, cudaStream_t st) {
+  const int64_t grid = (a.p.n + block - 1) / block;
+  if (grid == 0) return cudaSuccess;
+  const bool d3 = a.g.nz > 1;
+  if (a.f.nf == 3) advect_plain_kernel<float, Store, 3, true><<<(unsigned)grid, block, 0, st>>>(a);
+  else if (d3) advect_plain_kernel<float, Store, 2, true><<<(unsigned)grid, block, 0, st>>>(a);
+  else advect_plain_kernel<float, Store, 2, false><<<(unsigned)grid, block, 0, st>>>(a);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advect_plain(const StepArgs &a, int real, int storage, int block,
+                                cudaStream_t st) {
+  if (real == PG_POS_F64) return launch_advect_f64(a, storage, block, st);
+  switch (storage) {
+    case PG_F32: return launch_f32<float>(a, block, st);
+    case PG_F16S: return launch_f32<__half>(a, block, st);
+    case PG_BF16S: return launch_f32<__nv_bfloat16>(a, block, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace pg

@@ -1,0 +1,27 @@
+// advect_f64.cu -- FP64 instantiations of the plain advection chunk.
+// Compiled with -fmad=false: every multiply and add rounds separately, in the
+// order the source states, as in the FP64 definition of the step.
+#include "advect_plain.cuh"
+#include "pg_host.h"
+
+namespace pg {
+
+template <typename Store>
+static cudaError_t launch_f64(const StepArgs &a, int block, cudaStream_t st) {
+  const int64_t grid = (a.p.n + block - 1) / block;
+  if (grid == 0) return cudaSuccess;
+  const bool d3 = a.g.nz > 1;
+  if (a.f.nf == 3) advect_plain_kernel<double, Store, 3, true><<<(unsigned)grid, block, 0, st>>>(a);
+  else if (d3) advect_plain_kernel<double, Store, 2, true><<<(unsigned)grid, block, 0, st>>>(a);
+  else advect_plain_kernel<double, Store, 2, false><<<(unsigned)grid, block, 0, st>>>(a);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advect_f64(const StepArgs &a, int storage, int block, cudaStream_t st) {
+  if (storage == PG_F64) return launch_f64<double>(a, block, st);
+  if (storage == PG_F32) return launch_f64<float>(a, block, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace pg

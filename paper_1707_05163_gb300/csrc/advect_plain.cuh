@@ -1,0 +1,522 @@
+// advect_plain.cuh -- the fused advection step for lon/lat/depth positions.
+//
+// One thread owns one particle for a whole chunk of steps (Eq. 1, Sect.
+// 2.1.1): the particle state stays in registers, and so do the field values
+// at the corners of the particle's current cell for the two bracketing
+// snapshots.  A stage re-reads the field only when the particle has moved to
+// another cell or another pair of snapshots, so the four RK4 stages of a step
+// and consecutive steps inside one cell share one gather.  The values used
+// are the same ones a fresh gather would return, so the arithmetic is that of
+// the definition.
+//
+// Instantiated twice:
+//   Real = double  (compiled with -fmad=false): the FP64 path, which carries
+//     out the oracle's operations in the oracle's order, including the FP64
+//     time interpolation of every stage;
+//   Real = float: the FP32 path, where stage times are FP32 offsets inside
+//     the cached snapshot interval and no FP64 arithmetic runs per stage.
+#pragma once
+
+#include "pg_device.cuh"
+
+namespace pg {
+
+// ------------------------------------------------------------ node loads ---
+// Interleaved storage: node (k, j, i) holds its NF field values contiguously
+// (NF = 3 padded to 4), so one vector load fetches U, V[, W] of a corner.
+template <int NF> struct NodeStride { static constexpr int value = NF == 2 ? 2 : 4; };
+
+template <typename Real, int NF>
+__device__ __forceinline__ void load_node(const double *p, size_t node, const float *, Real (&v)[NF]) {
+  if constexpr (NF == 2) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p) + node);
+    v[0] = (Real)a.x; v[1] = (Real)a.y;
+  } else {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p) + 2 * node);
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 2 * node + 1);
+    v[0] = (Real)a.x; v[1] = (Real)a.y; v[2] = (Real)b.x;
+  }
+}
+
+template <typename Real, int NF>
+__device__ __forceinline__ void load_node(const float *p, size_t node, const float *, Real (&v)[NF]) {
+  if constexpr (NF == 2) {
+    const float2 a = __ldg(reinterpret_cast<const float2 *>(p) + node);
+    v[0] = (Real)a.x; v[1] = (Real)a.y;
+  } else {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p) + node);
+    v[0] = (Real)a.x; v[1] = (Real)a.y; v[2] = (Real)a.z;
+  }
+}
+
+// Quantised storage: value = float(code) * scale, rounded in FP32.
+template <typename Real, int NF>
+__device__ __forceinline__ void load_node(const __half *p, size_t node, const float *sc, Real (&v)[NF]) {
+  if constexpr (NF == 2) {
+    const __half2 a = __ldg(reinterpret_cast<const __half2 *>(p) + node);
+    v[0] = (Real)(__low2float(a) * sc[0]); v[1] = (Real)(__high2float(a) * sc[1]);
+  } else {
+    const uint2 a = __ldg(reinterpret_cast<const uint2 *>(p) + node);
+    const __half2 lo = *reinterpret_cast<const __half2 *>(&a.x);
+    const __half2 hi = *reinterpret_cast<const __half2 *>(&a.y);
+    v[0] = (Real)(__low2float(lo) * sc[0]); v[1] = (Real)(__high2float(lo) * sc[1]);
+    v[2] = (Real)(__low2float(hi) * sc[2]);
+  }
+}
+
+template <typename Real, int NF>
+__device__ __forceinline__ void load_node(const __nv_bfloat16 *p, size_t node, const float *sc, Real (&v)[NF]) {
+  if constexpr (NF == 2) {
+    const __nv_bfloat162 a = __ldg(reinterpret_cast<const __nv_bfloat162 *>(p) + node);
+    v[0] = (Real)(__low2float(a) * sc[0]); v[1] = (Real)(__high2float(a) * sc[1]);
+  } else {
+    const uint2 a = __ldg(reinterpret_cast<const uint2 *>(p) + node);
+    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162 *>(&a.x);
+    const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162 *>(&a.y);
+    v[0] = (Real)(__low2float(lo) * sc[0]); v[1] = (Real)(__high2float(lo) * sc[1]);
+    v[2] = (Real)(__low2float(hi) * sc[2]);
+  }
+}
+
+// ------------------------------------------------------- math per Real ---
+__device__ __forceinline__ double pg_fmod(double a, double b) { return fmod(a, b); }
+__device__ __forceinline__ float pg_fmod(float a, float b) { return fmodf(a, b); }
+__device__ __forceinline__ double pg_floor(double a) { return floor(a); }
+__device__ __forceinline__ float pg_floor(float a) { return floorf(a); }
+__device__ __forceinline__ double pg_sqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float pg_sqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double pg_fabs(double a) { return fabs(a); }
+__device__ __forceinline__ float pg_fabs(float a) { return fabsf(a); }
+// cos(lat in degrees)
+__device__ __forceinline__ double cos_deg(double lat) {
+  const double deg2rad = 3.14159265358979323846 / 180.0;
+  return cos(lat * deg2rad);
+}
+__device__ __forceinline__ float cos_deg(float lat) { return cospif(lat * (1.0f / 180.0f)); }
+
+template <typename Real> __device__ __forceinline__ const Real *axis(const GridArgs &g, int a);
+template <> __device__ __forceinline__ const double *axis<double>(const GridArgs &g, int a) {
+  return a == 0 ? g.lon : (a == 1 ? g.lat : g.depth);
+}
+template <> __device__ __forceinline__ const float *axis<float>(const GridArgs &g, int a) {
+  return a == 0 ? g.lonf : (a == 1 ? g.latf : g.depthf);
+}
+template <typename Real> __device__ __forceinline__ Real axis_x0(const GridArgs &g, int a);
+template <> __device__ __forceinline__ double axis_x0<double>(const GridArgs &g, int a) { return g.x0[a]; }
+template <> __device__ __forceinline__ float axis_x0<float>(const GridArgs &g, int a) { return g.x0f[a]; }
+template <typename Real> __device__ __forceinline__ Real axis_inv(const GridArgs &g, int a);
+template <> __device__ __forceinline__ double axis_inv<double>(const GridArgs &g, int a) { return g.inv_d[a]; }
+template <> __device__ __forceinline__ float axis_inv<float>(const GridArgs &g, int a) { return g.inv_df[a]; }
+
+// Full search on one axis: the largest i <= n-2 with x[i] <= p, given that
+// x[0] <= p <= x[n-1].  Uniform axes start from floor((p - x0) / dx) and
+// correct against the stored nodes; others use bisection.
+template <typename Real>
+__device__ __forceinline__ int axis_search(const GridArgs &g, int a, int n, Real p) {
+  const Real *x = axis<Real>(g, a);
+  int i;
+  if (g.uni[a]) {
+    const Real f = pg_floor((p - axis_x0<Real>(g, a)) * axis_inv<Real>(g, a));
+    i = f < (Real)0 ? 0 : (f > (Real)(n - 2) ? n - 2 : (int)f);
+    while (i > 0 && x[i] > p) --i;
+    while (i < n - 2 && x[i + 1] <= p) ++i;
+  } else {
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+      const int mid = lo + (hi - lo) / 2;
+      if (x[mid] <= p) lo = mid; else hi = mid;
+    }
+    i = lo;
+  }
+  return i;
+}
+
+// ---------------------------------------------------------- the sampler ---
+template <typename Real, typename Store, int NF, bool D3>
+struct Sampler {
+  static constexpr int NC = D3 ? 8 : 4;
+  // cached cell (ci = -1: none) and its bounds
+  int ci, ci1, cj, ck;
+  Real xlo, xhi, ylo, yhi, zlo, zhi;
+  Real rx, ry, rz;            // 1 / (hi - lo), FP32 path only
+  // cached snapshot interval and the snapshots whose corners are held
+  int s0, s1;
+  int gi, gj, gk, gs0, gs1;   // what `v` currently holds (gi = -1: nothing)
+  double ta, tb;              // interval bounds, FP64 path: wrapped; FP32 path: ta unwrapped
+  float span, rspan;          // FP32 path
+  Real v[2][NF][NC];
+
+  __device__ __forceinline__ void reset() {
+    ci = -1; cj = -1; ck = -1; s0 = -1; gi = -1;
+  }
+};
+
+// Locate p on the longitude axis, using and refreshing the cache.
+// Returns false when the position is out of the domain.
+template <typename Real, typename Store, int NF, bool D3>
+__device__ __forceinline__ bool locate_lon(const GridArgs &g, Sampler<Real, Store, NF, D3> &c,
+                                           Real p, Real &xi) {
+  Real q = p;
+  const Real *x = axis<Real>(g, 0);
+  if (g.periodic) {
+    if (!isfinite(p)) return false;
+    const Real x0 = x[0];
+    Real r = pg_fmod(p - x0, (Real)360);
+    if (r < (Real)0) r += (Real)360;
+    if (r >= (Real)360) r -= (Real)360;
+    q = x0 + r;
+  } else if (!(p >= x[0] && p <= x[g.nx - 1])) {
+    return false;
+  }
+  const bool last = c.ci == g.nx - 2 && !g.periodic;
+  if (!(c.ci >= 0 && q >= c.xlo && (q < c.xhi || (last && q == c.xhi)))) {
+    if (g.periodic && q >= x[g.nx - 1]) {
+      c.ci = g.nx - 1; c.ci1 = 0;
+      c.xlo = x[g.nx - 1];
+      c.xhi = (Real)g.lon_end;
+    } else {
+      const int i = axis_search<Real>(g, 0, g.nx, q);
+      c.ci = i; c.ci1 = i + 1;
+      c.xlo = x[i]; c.xhi = x[i + 1];
+    }
+    c.rx = (Real)1 / (c.xhi - c.xlo);
+  }
+  if constexpr (sizeof(Real) == 8) xi = (q - c.xlo) / (c.xhi - c.xlo);
+  else xi = (q - c.xlo) * c.rx;
+  return true;
+}
+
+template <typename Real>
+__device__ __forceinline__ bool locate_axis(const GridArgs &g, int a, int n, int &ci, Real &lo,
+                                            Real &hi, Real &rinv, Real p, Real &xi) {
+  const Real *x = axis<Real>(g, a);
+  if (!(p >= x[0] && p <= x[n - 1])) return false;
+  const bool last = ci == n - 2;
+  if (!(ci >= 0 && p >= lo && (p < hi || (last && p == hi)))) {
+    const int i = axis_search<Real>(g, a, n, p);
+    ci = i; lo = x[i]; hi = x[i + 1];
+    rinv = (Real)1 / (hi - lo);
+  }
+  if constexpr (sizeof(Real) == 8) xi = (p - lo) / (hi - lo);
+  else xi = (p - lo) * rinv;
+  return true;
+}
+
+// Snapshot interval for time t in FP64 (same rules as the definition: the
+// largest s <= nt-2 with T[s] <= t; periodic fields reduce t into
+// [T0, T0 + period) and interpolate from the last snapshot to the first
+// after T[nt-1]).  Writes s0, s1, wrapped tt and the interval bounds.
+__device__ __forceinline__ bool time_interval(const FieldArgs &f, double t, int &s0, int &s1,
+                                              double &tt, double &ta, double &tb) {
+  const double *T = f.times;
+  const int nt = f.nt;
+  tt = t;
+  if (f.period > 0.0) {
+    double r = fmod(t - T[0], f.period);
+    if (r < 0.0) r += f.period;
+    tt = T[0] + r;
+    if (tt >= T[nt - 1]) {
+      s0 = nt - 1; s1 = 0;
+      ta = T[nt - 1]; tb = T[0] + f.period;
+      return true;
+    }
+  }
+  if (!(tt >= T[0] && tt <= T[nt - 1])) return false;
+  int lo = 0, hi = nt - 1;
+  if (s0 >= 0 && s0 <= nt - 2 && T[s0] <= tt && (tt < T[s0 + 1] || (s0 == nt - 2 && tt == T[nt - 1]))) {
+    lo = s0;
+  } else {
+    while (hi - lo > 1) {
+      const int mid = lo + (hi - lo) / 2;
+      if (T[mid] <= tt) lo = mid; else hi = mid;
+    }
+  }
+  s0 = lo; s1 = lo + 1;
+  ta = T[lo]; tb = T[lo + 1];
+  return true;
+}
+
+// Gather the corner values of the cached cell for snapshots s0 and s1.
+template <typename Real, typename Store, int NF, bool D3>
+__device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
+                                       bool steady) {
+  const GridArgs &g = a.g;
+  const int nslab = steady ? 1 : 2;
+#pragma unroll
+  for (int sl = 0; sl < 2; ++sl) {
+    if (sl >= nslab) break;
+    const int s = sl == 0 ? c.s0 : c.s1;
+    const Store *base = reinterpret_cast<const Store *>(a.f.tab[s]);
+    if (base == nullptr) {
+      atomicCAS(a.err, 0, (int)DEVERR_SLAB_MISSING);
+      return false;
+    }
+    float sc[3] = {1.f, 1.f, 1.f};
+    if (a.f.scales != nullptr) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) sc[f] = a.f.scales[s * NF + f];
+    }
+#pragma unroll
+    for (int kk = 0; kk < (D3 ? 2 : 1); ++kk) {
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+#pragma unroll
+        for (int ii = 0; ii < 2; ++ii) {
+          const size_t node = ((size_t)(c.ck + kk) * g.ny + (size_t)(c.cj + jj)) * g.nx +
+                              (size_t)(ii ? c.ci1 : c.ci);
+          Real vv[NF];
+          load_node<Real, NF>(base, node, sc, vv);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) c.v[sl][f][kk * 4 + jj * 2 + ii] = vv[f];
+        }
+      }
+    }
+  }
+  c.gi = c.ci; c.gj = c.cj; c.gk = c.ck; c.gs0 = c.s0; c.gs1 = c.s1;
+  return true;
+}
+
+// Bilinear weights applied as (w00 f00 + w10 f10) + (w11 f11 + w01 f01);
+// trilinear is linear in zeta between the two levels.
+template <typename Real, int NC>
+__device__ __forceinline__ Real interp_space(const Real (&v)[NC], Real xi, Real eta, Real zeta) {
+  const Real w00 = ((Real)1 - xi) * ((Real)1 - eta);
+  const Real w10 = xi * ((Real)1 - eta);
+  const Real w11 = xi * eta;
+  const Real w01 = ((Real)1 - xi) * eta;
+  const Real a = (w00 * v[0] + w10 * v[1]) + (w11 * v[3] + w01 * v[2]);
+  if constexpr (NC == 4) {
+    return a;
+  } else {
+    const Real b = (w00 * v[4] + w10 * v[5]) + (w11 * v[7] + w01 * v[6]);
+    return ((Real)1 - zeta) * a + zeta * b;
+  }
+}
+
+// Time of the current step.  FP64 path: `t` is the exact step start.  FP32
+// path: the step start is t + k * dt, known to the kernel only as `d`, its
+// FP32 offset inside the cached snapshot interval; the FP64 value is formed
+// only when a stage leaves that interval.
+struct Clock {
+  double t, dt;
+  int k;
+  float d;
+  __device__ __forceinline__ double start() const { return t + (double)k * dt; }
+};
+
+// Velocity in position units per second at a stage.  FP64 path: the stage
+// time is t0 + off evaluated in FP64.  FP32 path: off is added to the FP32
+// offset d0 = t0 - ta of the step start inside the cached interval.
+// Returns 0 or a particle status (PG_OOB_*, PG_NAN); -1 for an internal
+// failure already recorded in a.err.
+template <typename Real, typename Store, int NF, bool D3>
+__device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
+                                        Clock &ck, Real off, Real lon, Real lat, Real dep,
+                                        Real (&vel)[3]) {
+  const GridArgs &g = a.g;
+  Real xi, eta, zeta = (Real)0;
+  if (!locate_lon(g, c, lon, xi)) return 1;
+  if (!locate_axis<Real>(g, 1, g.ny, c.cj, c.ylo, c.yhi, c.ry, lat, eta)) return 1;
+  if constexpr (D3) {
+    if (!locate_axis<Real>(g, 2, g.nz, c.ck, c.zlo, c.zhi, c.rz, dep, zeta)) return 2;
+  } else {
+    c.ck = 0;
+  }
+  const bool steady = a.f.nt == 1;
+  Real tau = (Real)0;
+  if (!steady) {
+    if constexpr (sizeof(Real) == 8) {
+      const double ts = ck.t + (double)off;
+      double tt, ta, tb;
+      int s0 = c.s0, s1 = c.s1;
+      if (!time_interval(a.f, ts, s0, s1, tt, ta, tb)) {
+        atomicCAS(a.err, 0, (int)DEVERR_TIME_RANGE);
+        return -1;
+      }
+      c.s0 = s0; c.s1 = s1;
+      tau = (Real)((tt - ta) / (tb - ta));
+    } else {
+      float d = ck.d + (float)off;
+      if (!(c.s0 >= 0 && d >= 0.f && d <= c.span)) {
+        const double t0 = ck.start();
+        const double ts = t0 + (double)off;
+        double tt, ta, tb;
+        int s0 = c.s0, s1 = c.s1;
+        if (!time_interval(a.f, ts, s0, s1, tt, ta, tb)) {
+          atomicCAS(a.err, 0, (int)DEVERR_TIME_RANGE);
+          return -1;
+        }
+        c.s0 = s0; c.s1 = s1;
+        c.ta = ts - (tt - ta);              // interval start in unwrapped time
+        c.span = (float)(tb - ta);
+        c.rspan = 1.0f / c.span;
+        d = (float)(tt - ta);
+        ck.d = (float)(t0 - c.ta);
+      }
+      tau = (Real)fminf(d * c.rspan, 1.0f);
+    }
+  } else {
+    c.s0 = 0; c.s1 = 0;
+  }
+  if (c.gi != c.ci || c.gj != c.cj || c.gk != c.ck || c.gs0 != c.s0 || c.gs1 != c.s1 ||
+      c.gi < 0) {
+    if (!gather(a, c, steady)) return -1;
+  }
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    Real val = interp_space<Real, Sampler<Real, Store, NF, D3>::NC>(c.v[0][f], xi, eta, zeta);
+    if (!steady) {
+      const Real b = interp_space<Real, Sampler<Real, Store, NF, D3>::NC>(c.v[1][f], xi, eta, zeta);
+      val = val + (b - val) * tau;
+    }
+    if (!(val == val)) return 3;
+    vel[f] = val;
+  }
+  if constexpr (NF == 2) vel[2] = (Real)0;
+  if (g.mesh == 1) {
+    vel[0] = vel[0] / ((Real)a.k.deg_m * cos_deg(lat));
+    vel[1] = vel[1] / (Real)a.k.deg_m;
+  }
+  return 0;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real wrap_lon(Real p, Real x0) {
+  Real r = pg_fmod(p - x0, (Real)360);
+  if (r < (Real)0) r += (Real)360;
+  if (r >= (Real)360) r -= (Real)360;
+  return x0 + r;
+}
+
+template <typename Real>
+__device__ __forceinline__ int out_of_domain(const GridArgs &g, Real lon, Real lat, Real dep,
+                                             bool d3) {
+  const Real *X = axis<Real>(g, 0);
+  const Real *Y = axis<Real>(g, 1);
+  if (!g.periodic && !(lon >= X[0] && lon <= X[g.nx - 1])) return 1;
+  if (g.periodic && !(lon == lon)) return 1;
+  if (!(lat >= Y[0] && lat <= Y[g.ny - 1])) return 1;
+  if (d3) {
+    const Real *Z = axis<Real>(g, 2);
+    if (!(dep >= Z[0] && dep <= Z[g.nz - 1])) return 2;
+  }
+  return 0;
+}
+
+// One step of Eq. 1.  Returns 0 and updates (lon, lat, dep) on success.
+template <typename Real, typename Store, int NF, bool D3>
+__device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
+                                        Clock &ck, Real &lon, Real &lat, Real &dep, Real hr,
+                                        uint64_t id, uint32_t stp) {
+  Real k1[3], k2[3], k3[3], k4[3];
+  Real nlon, nlat, ndep;
+  int r;
+  if (a.k.scheme == 0) {
+    if ((r = velocity(a, c, ck, (Real)0, lon, lat, dep, k1))) return r;
+    nlon = lon + k1[0] * hr;
+    nlat = lat + k1[1] * hr;
+    ndep = dep + k1[2] * hr;
+  } else {
+    const Real half = (Real)0.5 * hr;
+    if ((r = velocity(a, c, ck, (Real)0, lon, lat, dep, k1))) return r;
+    if ((r = velocity(a, c, ck, half, lon + k1[0] * half, lat + k1[1] * half,
+                      dep + k1[2] * half, k2))) return r;
+    if ((r = velocity(a, c, ck, half, lon + k2[0] * half, lat + k2[1] * half,
+                      dep + k2[2] * half, k3))) return r;
+    if ((r = velocity(a, c, ck, hr, lon + k3[0] * hr, lat + k3[1] * hr, dep + k3[2] * hr,
+                      k4))) return r;
+    nlon = lon + (k1[0] + (Real)2 * k2[0] + (Real)2 * k3[0] + k4[0]) / (Real)6 * hr;
+    nlat = lat + (k1[1] + (Real)2 * k2[1] + (Real)2 * k3[1] + k4[1]) / (Real)6 * hr;
+    ndep = dep + (k1[2] + (Real)2 * k2[2] + (Real)2 * k3[2] + k4[2]) / (Real)6 * hr;
+  }
+  if (a.k.beh & 1u) {
+    Real n1, n2;
+    normal_pair(a.k.seed, id, stp, n1, n2);
+    const Real sigma = pg_sqrt((Real)2 * (Real)a.k.kh * pg_fabs(hr));
+    Real dx = sigma * n1, dy = sigma * n2;
+    if (a.g.mesh == 1) {
+      dx = dx / ((Real)a.k.deg_m * cos_deg(nlat));
+      dy = dy / (Real)a.k.deg_m;
+    }
+    nlon = nlon + dx;
+    nlat = nlat + dy;
+  }
+  if (a.k.beh & 2u) ndep = ndep + (Real)a.k.w_sink * hr;
+  if (a.g.periodic) nlon = wrap_lon<Real>(nlon, axis<Real>(a.g, 0)[0]);
+  if ((r = out_of_domain<Real>(a.g, nlon, nlat, ndep, D3))) return r;
+  lon = nlon; lat = nlat; dep = ndep;
+  return 0;
+}
+
+// The chunk kernel: each thread advances one particle while its time is
+// before t_stop and t_end (in the direction of dt), shortening only the step
+// that lands on t_end.
+template <typename Real, typename Store, int NF, bool D3>
+__global__ void advect_plain_kernel(StepArgs a) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long done = 0;
+  if (p < a.p.n && a.p.status[p] == 0) {
+    Real *X = reinterpret_cast<Real *>(a.p.x);
+    Real *Y = reinterpret_cast<Real *>(a.p.y);
+    Real *Z = reinterpret_cast<Real *>(a.p.z);
+    Real lon = X[p], lat = Y[p], dep = Z[p];
+    double t = a.p.time[p];
+    uint32_t stp = a.p.step[p];
+    const uint64_t id = a.p.id[p];
+    uint8_t st = 0;
+    Sampler<Real, Store, NF, D3> c;
+    c.reset();
+    const double sgn = a.dt > 0.0 ? 1.0 : -1.0;
+    Clock ck;
+    if constexpr (sizeof(Real) == 8) {
+      // FP64: the definition's loop, time accumulated step by step.
+      while (sgn * (a.t_stop - t) > 0.0 && sgn * (a.t_end - t) > 0.0) {
+        double h = a.dt;
+        if (sgn * (a.t_end - t) < sgn * h) h = a.t_end - t;
+        ck.t = t;
+        const int r = step_one(a, c, ck, lon, lat, dep, (Real)h, id, stp);
+        if (r > 0) { st = (uint8_t)r; break; }
+        if (r < 0) break;
+        t = t + h;
+        ++stp;
+        ++done;
+      }
+    } else {
+      // FP32: the step count of this chunk is fixed up front; step k starts
+      // at t + k dt (exact for times and steps in whole seconds), and only
+      // a step that lands on t_end is shortened.
+      const double tl = sgn > 0.0 ? fmin(a.t_stop, a.t_end) : fmax(a.t_stop, a.t_end);
+      int n = 0;
+      if (sgn * (tl - t) > 0.0) n = (int)ceil((tl - t) / a.dt);
+      double hlast = a.dt;
+      if (n > 0 && sgn * (a.t_end - (t + (double)(n - 1) * a.dt)) < sgn * a.dt)
+        hlast = a.t_end - (t + (double)(n - 1) * a.dt);
+      const float hf = (float)a.dt;
+      ck.t = t; ck.dt = a.dt; ck.k = 0;
+      ck.d = 0.f;
+      int k = 0;
+      for (; k < n; ++k) {
+        ck.k = k;
+        const float h = (k == n - 1) ? (float)hlast : hf;
+        const int r = step_one(a, c, ck, lon, lat, dep, (Real)h, id, stp);
+        if (r > 0) { st = (uint8_t)r; break; }
+        if (r < 0) break;
+        ++stp;
+        ck.d += h;
+      }
+      done = (unsigned long long)k;
+      if (k == n && n > 0) t = (hlast != a.dt) ? a.t_end : t + (double)n * a.dt;
+      else t = t + (double)k * a.dt;
+    }
+    X[p] = lon; Y[p] = lat; Z[p] = dep;
+    a.p.time[p] = t;
+    a.p.step[p] = stp;
+    a.p.status[p] = st;
+  }
+  // one atomic per warp for the particle-step counter
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);
+  if ((threadIdx.x & 31) == 0 && done) atomicAdd(a.steps_done, done);
+}
+
+}  // namespace pg

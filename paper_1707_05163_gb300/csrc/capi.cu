@@ -1,0 +1,1184 @@
+// capi.cu -- the C ABI: field sets, kernels, particle sets and the time loop.
+//
+// The objects follow the FieldSet / ParticleSet / Kernel / execute statement
+// of the problem in Lange & van Sebille, "Parcels v0.9" (Sect. 2.1, 2.2, 2.4
+// and 3).  The time loop advances particles in chunks of steps (one kernel
+// launch each); chunks end at output times, at re-sort times and, for
+// streamed fields, at snapshot times, so that the snapshots a chunk needs are
+// resident before it starts while the next one uploads on a side stream.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <limits>
+
+#include "pg_host.h"
+
+namespace pg {
+
+static thread_local std::string g_err;
+static int64_t g_alloc_limit = -1;      // test hook: fail allocations beyond this
+static int64_t g_alloc_bytes = 0;
+static std::atomic<long long> g_launches{0};
+
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void set_error(const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (g_alloc_limit >= 0 && g_alloc_bytes + (int64_t)bytes > g_alloc_limit)
+    return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_alloc_bytes += (int64_t)bytes;
+  return e;
+}
+void dev_free(void *p) {
+  if (p) cudaFree(p);
+}
+
+cudaError_t launch_resort(pg_pset *ps, cudaStream_t st, int64_t *n_alive);
+cudaError_t launch_moments(const pg_pset *ps, double *out7, cudaStream_t st);
+
+}  // namespace pg
+
+using namespace pg;
+
+#define CU(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      set_error("%s failed: %s", #call, cudaGetErrorString(e_));                      \
+      return e_ == cudaErrorMemoryAllocation ? PG_ERR_NOMEM : PG_ERR_CUDA;            \
+    }                                                                                 \
+  } while (0)
+
+#define ARG(cond, msg)                                                                \
+  do {                                                                                \
+    if (!(cond)) {                                                                    \
+      set_error("invalid argument: %s", msg);                                         \
+      return PG_ERR_ARG;                                                              \
+    }                                                                                 \
+  } while (0)
+
+namespace {
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool strictly_increasing(const double *x, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(x[i])) return false;
+  for (int i = 1; i < n; ++i)
+    if (!(x[i] > x[i - 1])) return false;
+  return true;
+}
+
+// Uniform spacing test: every node within 1e-9 of a spacing of the ideal one.
+bool uniform_axis(const std::vector<double> &x, double &x0, double &inv_d) {
+  const int n = (int)x.size();
+  x0 = x[0];
+  if (n < 2) { inv_d = 0.0; return false; }
+  const double d = (x[n - 1] - x[0]) / (n - 1);
+  for (int i = 0; i < n; ++i)
+    if (std::fabs(x[i] - (x[0] + i * d)) > 1e-9 * d) { inv_d = 1.0 / d; return false; }
+  inv_d = 1.0 / d;
+  return true;
+}
+
+__global__ void f64_to_f32_kernel(const double *src, float *dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+__global__ void f32_to_f64_kernel(const float *src, double *dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+__global__ void fill_f64_kernel(double *dst, double v, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = v;
+}
+__global__ void iota_u64_kernel(uint64_t *dst, uint64_t base, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = base + (uint64_t)i;
+}
+
+int grid_for(int64_t n, int sm) {
+  int64_t g = (n + 255) / 256;
+  const int64_t cap = (int64_t)sm * 16;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// Copy n doubles (host or device) into a device array of the position type.
+pg_status upload_coord(const double *src, int64_t n, void *dst, int pos, double fill, int sm,
+                       cudaStream_t st) {
+  if (n == 0) return PG_OK;
+  if (pos == PG_POS_F64) {
+    if (src) {
+      CU(cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyDefault, st));
+    } else {
+      fill_f64_kernel<<<grid_for(n, sm), 256, 0, st>>>((double *)dst, fill, n);
+      note_launches(1);
+      CU(cudaGetLastError());
+    }
+    return PG_OK;
+  }
+  if (!src) {
+    std::vector<float> h((size_t)n, (float)fill);
+    CU(cudaMemcpyAsync(dst, h.data(), n * 4, cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));
+    return PG_OK;
+  }
+  if (!is_device_ptr(src)) {
+    std::vector<float> h((size_t)n);
+    for (int64_t i = 0; i < n; ++i) h[i] = (float)src[i];
+    CU(cudaMemcpyAsync(dst, h.data(), n * 4, cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));
+    return PG_OK;
+  }
+  f64_to_f32_kernel<<<grid_for(n, sm), 256, 0, st>>>(src, (float *)dst, n);
+  note_launches(1);
+  CU(cudaGetLastError());
+  return PG_OK;
+}
+
+}  // namespace
+
+namespace pg {
+pg_status alloc_arrays(PsetArrays &A, int pos, int64_t cap) {
+  const size_t n = (size_t)std::max<int64_t>(cap, 1);
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void **p, size_t b) {
+    if (e == cudaSuccess) e = dev_alloc(p, b);
+  };
+  if (pos == PG_POS_CELL) {
+    al((void **)&A.ci, n * 4); al((void **)&A.cj, n * 4); al((void **)&A.ck, n * 4);
+    al((void **)&A.fx, n * 4); al((void **)&A.fy, n * 4); al((void **)&A.fz, n * 4);
+  } else {
+    const size_t el = pos_elem(pos);
+    al(&A.x, n * el); al(&A.y, n * el); al(&A.z, n * el);
+  }
+  al((void **)&A.time, n * 8);
+  al((void **)&A.id, n * 8);
+  al((void **)&A.step, n * 4);
+  al((void **)&A.status, n);
+  if (e != cudaSuccess) {
+    A.free_all();
+    cudaGetLastError();
+    set_error("device allocation of %lld particles failed: %s", (long long)cap,
+              cudaGetErrorString(e));
+    return PG_ERR_NOMEM;
+  }
+  return PG_OK;
+}
+
+}  // namespace pg
+
+namespace {
+
+PsetArrays arrays_of(const pg_pset *ps) {
+  PsetArrays A;
+  A.x = ps->x; A.y = ps->y; A.z = ps->z;
+  A.ci = ps->ci; A.cj = ps->cj; A.ck = ps->ck;
+  A.fx = ps->fx; A.fy = ps->fy; A.fz = ps->fz;
+  A.time = ps->time; A.id = ps->id; A.step = ps->step; A.status = ps->status;
+  return A;
+}
+
+void set_arrays(pg_pset *ps, const PsetArrays &A) {
+  ps->x = A.x; ps->y = A.y; ps->z = A.z;
+  ps->ci = A.ci; ps->cj = A.cj; ps->ck = A.ck;
+  ps->fx = A.fx; ps->fy = A.fy; ps->fz = A.fz;
+  ps->time = A.time; ps->id = A.id; ps->step = A.step; ps->status = A.status;
+}
+
+GridArgs grid_args(const pg_fieldset *fs) {
+  GridArgs g;
+  g.nx = fs->nx; g.ny = fs->ny; g.nz = fs->nz;
+  g.mesh = fs->mesh; g.periodic = fs->periodic;
+  g.lon = fs->d_axes64; g.lat = fs->d_axes64 + fs->nx; g.depth = fs->d_axes64 + fs->nx + fs->ny;
+  g.lonf = fs->d_axes32; g.latf = fs->d_axes32 + fs->nx; g.depthf = fs->d_axes32 + fs->nx + fs->ny;
+  for (int a = 0; a < 3; ++a) {
+    g.uni[a] = fs->uni[a];
+    g.x0[a] = fs->x0[a];
+    g.inv_d[a] = fs->inv_d[a];
+    g.x0f[a] = (float)fs->x0[a];
+    g.inv_df[a] = (float)fs->inv_d[a];
+  }
+  g.lon_end = fs->lon[0] + 360.0;
+  return g;
+}
+
+// ---------------------------------------------------------------- streaming
+
+// Snapshot index for a (possibly periodic) snapshot counter m: periodic
+// fields repeat every nt snapshots.
+int snap_of(const pg_fieldset *fs, long long m) {
+  const long long nt = fs->nt;
+  long long r = m % nt;
+  if (r < 0) r += nt;
+  return (int)r;
+}
+
+// Unwrapped snapshot counter m with T(m) <= t < T(m+1), where
+// T(m) = times[m mod nt] + floor(m / nt) * period (periodic) or times[m].
+long long snap_counter(const pg_fieldset *fs, double t) {
+  const int nt = fs->nt;
+  double base = 0.0;
+  long long turns = 0;
+  double tt = t;
+  if (fs->period > 0.0) {
+    double r = std::fmod(t - fs->times[0], fs->period);
+    if (r < 0.0) r += fs->period;
+    turns = (long long)std::floor((t - fs->times[0] - r) / fs->period + 0.5);
+    tt = fs->times[0] + r;
+    base = (double)turns;
+  }
+  (void)base;
+  int s = (int)(std::upper_bound(fs->times.begin(), fs->times.end(), tt) - fs->times.begin()) - 1;
+  if (s < 0) s = 0;
+  if (fs->period <= 0.0 && s > nt - 2) s = std::max(0, nt - 2);
+  return turns * nt + s;
+}
+
+double snap_time(const pg_fieldset *fs, long long m) {
+  const long long nt = fs->nt;
+  long long q = m >= 0 ? m / nt : -((-m + nt - 1) / nt);
+  const int s = (int)(m - q * nt);
+  return fs->times[s] + (fs->period > 0.0 ? (double)q * fs->period : 0.0);
+}
+
+pg_status upload_to_slot(pg_fieldset *fs, Slot &sl, int s) {
+  cudaStream_t side = fs->side;
+  CU(cudaStreamWaitEvent(side, sl.free, 0));
+  const size_t el = fs->src_dtype == PG_F64 ? 8 : 4;
+  const size_t bytes = (size_t)fs->nfields * fs->nodes * el;
+  const void *src = nullptr;
+  if (fs->cb) {
+    CU(cudaEventSynchronize(fs->stage_free));
+    if (fs->cb(fs->cb_user, s, fs->h_pinned, bytes) != 0) {
+      set_error("snapshot callback failed for snapshot %d", s);
+      return PG_ERR_CALLBACK;
+    }
+    CU(cudaMemcpyAsync(fs->d_stage, fs->h_pinned, bytes, cudaMemcpyHostToDevice, side));
+    CU(cudaEventRecord(fs->stage_free, side));
+    src = fs->d_stage;
+    fs->upload_h2d_bytes += (int64_t)bytes;
+  } else {
+    const void *p = fs->src_ptrs[s];
+    if (is_device_ptr(p)) {
+      src = p;
+    } else {
+      CU(cudaMemcpyAsync(fs->d_stage, p, bytes, cudaMemcpyHostToDevice, side));
+      src = fs->d_stage;
+      fs->upload_h2d_bytes += (int64_t)bytes;
+    }
+  }
+  ++fs->uploads;
+  CU(launch_repack(src, fs->src_dtype, fs->nfields, fs->nodes, sl.buf, fs->storage, sl.scales,
+                   fs->d_amax, fs->sm_count, side));
+  CU(cudaEventRecord(sl.ready, side));
+  sl.s = s;
+  return PG_OK;
+}
+
+// Make the snapshots `need` resident (uploading the missing ones on the side
+// stream), then start uploading `prefetch` into a slot no chunk needs now.
+pg_status ensure_slots(pg_fieldset *fs, const std::vector<int> &need, int prefetch,
+                       cudaStream_t st) {
+  auto find = [&](int s) {
+    for (int q = 0; q < 4; ++q)
+      if (fs->slot[q].s == s) return q;
+    return -1;
+  };
+  auto needed = [&](int q) {
+    return std::find(need.begin(), need.end(), fs->slot[q].s) != need.end();
+  };
+  for (int s : need) {
+    if (find(s) >= 0) continue;
+    int q = -1;
+    for (int c = 0; c < 4 && q < 0; ++c)
+      if (!needed(c) && fs->slot[c].s != prefetch) q = c;
+    for (int c = 0; c < 4 && q < 0; ++c)
+      if (!needed(c)) q = c;
+    if (q < 0) {
+      set_error("streamed field needs more than four resident snapshots per chunk");
+      return PG_ERR_UNSUPPORTED;
+    }
+    pg_status r = upload_to_slot(fs, fs->slot[q], s);
+    if (r) return r;
+  }
+  // device table: resident slots only
+  std::vector<const void *> tab((size_t)fs->nt, nullptr);
+  for (int s : need) {
+    const int q = find(s);
+    CU(cudaStreamWaitEvent(st, fs->slot[q].ready, 0));
+    tab[s] = fs->slot[q].buf;
+    CU(cudaMemcpyAsync(fs->d_scales + (size_t)s * fs->nfields, fs->slot[q].scales,
+                       sizeof(float) * fs->nfields, cudaMemcpyDeviceToDevice, st));
+  }
+  CU(cudaMemcpyAsync(fs->d_tab, tab.data(), sizeof(void *) * fs->nt, cudaMemcpyHostToDevice, st));
+  if (prefetch >= 0 && find(prefetch) < 0) {
+    int q = -1;
+    for (int c = 0; c < 4 && q < 0; ++c)
+      if (!needed(c)) q = c;
+    if (q >= 0) {
+      pg_status r = upload_to_slot(fs, fs->slot[q], prefetch);
+      if (r) return r;
+    }
+  }
+  return PG_OK;
+}
+
+void mark_slots_used(pg_fieldset *fs, const std::vector<int> &need, cudaStream_t st) {
+  for (int q = 0; q < 4; ++q)
+    if (std::find(need.begin(), need.end(), fs->slot[q].s) != need.end())
+      cudaEventRecord(fs->slot[q].free, st);
+}
+
+void free_streaming(pg_fieldset *fs) {
+  for (auto &sl : fs->slot) {
+    dev_free(sl.buf);
+    dev_free(sl.scales);
+    if (sl.ready) cudaEventDestroy(sl.ready);
+    if (sl.free) cudaEventDestroy(sl.free);
+    sl = Slot();
+  }
+  if (fs->h_pinned) cudaFreeHost(fs->h_pinned);
+  fs->h_pinned = nullptr;
+  if (fs->side) cudaStreamDestroy(fs->side);
+  fs->side = nullptr;
+  if (fs->stage_free) cudaEventDestroy(fs->stage_free);
+  fs->stage_free = nullptr;
+  fs->streaming = false;
+  fs->cb = nullptr;
+  fs->src_ptrs.clear();
+}
+
+void free_resident(pg_fieldset *fs) {
+  for (void *p : fs->slabs) dev_free(p);
+  fs->slabs.clear();
+}
+
+}  // namespace
+
+// ======================================================================== ABI
+
+extern "C" {
+
+const char *pg_last_error(void) { return g_err.c_str(); }
+
+const char *pg_version(void) { return "parcels-gb300 0.1 (sm_103a)"; }
+
+pg_status pg_debug_set_alloc_limit(int64_t bytes) {
+  g_alloc_limit = bytes < 0 ? -1 : g_alloc_bytes + bytes;
+  return PG_OK;
+}
+
+pg_status pg_fieldset_create(const pg_grid *grid, int mesh, int periodic_lon, int nfields,
+                             int storage, pg_fieldset **out) {
+  clear_error();
+  ARG(grid && out, "grid and out must not be NULL");
+  ARG(grid->nx >= 2 && grid->ny >= 2 && grid->nz >= 1, "need nx >= 2, ny >= 2, nz >= 1");
+  ARG(grid->lon && grid->lat && (grid->nz == 1 || grid->depth), "axis pointers must be set");
+  ARG(strictly_increasing(grid->lon, grid->nx), "lon must be finite and strictly increasing");
+  ARG(strictly_increasing(grid->lat, grid->ny), "lat must be finite and strictly increasing");
+  ARG(grid->nz == 1 || strictly_increasing(grid->depth, grid->nz),
+      "depth must be finite and strictly increasing");
+  ARG(mesh == PG_FLAT || mesh == PG_SPHERICAL, "mesh must be PG_FLAT or PG_SPHERICAL");
+  ARG(!periodic_lon || mesh == PG_SPHERICAL, "periodic lon needs a spherical mesh");
+  ARG(!periodic_lon || grid->lon[grid->nx - 1] - grid->lon[0] < 360.0,
+      "periodic lon axis must span less than 360 degrees");
+  ARG(nfields == 2 || (nfields == 3 && grid->nz > 1), "nfields must be 2, or 3 with nz > 1");
+  ARG(storage >= PG_F64 && storage <= PG_BF16S, "unknown storage");
+  auto *fs = new pg_fieldset();
+  CU(cudaGetDevice(&fs->device));
+  CU(cudaDeviceGetAttribute(&fs->sm_count, cudaDevAttrMultiProcessorCount, fs->device));
+  fs->nx = grid->nx; fs->ny = grid->ny; fs->nz = grid->nz;
+  fs->mesh = mesh; fs->periodic = periodic_lon ? 1 : 0;
+  fs->nfields = nfields; fs->storage = storage;
+  fs->lon.assign(grid->lon, grid->lon + grid->nx);
+  fs->lat.assign(grid->lat, grid->lat + grid->ny);
+  if (grid->nz > 1) fs->depth.assign(grid->depth, grid->depth + grid->nz);
+  else fs->depth.assign(1, grid->depth ? grid->depth[0] : 0.0);
+  fs->uni[0] = uniform_axis(fs->lon, fs->x0[0], fs->inv_d[0]);
+  fs->uni[1] = uniform_axis(fs->lat, fs->x0[1], fs->inv_d[1]);
+  fs->uni[2] = grid->nz > 1 ? uniform_axis(fs->depth, fs->x0[2], fs->inv_d[2]) : 0;
+  fs->nodes = (size_t)fs->nx * fs->ny * fs->nz;
+  fs->slab_bytes = fs->nodes * (nfields == 2 ? 2 : 4) * storage_elem(storage);
+  const int na = fs->nx + fs->ny + fs->nz;
+  std::vector<double> ax;
+  ax.insert(ax.end(), fs->lon.begin(), fs->lon.end());
+  ax.insert(ax.end(), fs->lat.begin(), fs->lat.end());
+  ax.insert(ax.end(), fs->depth.begin(), fs->depth.end());
+  std::vector<float> axf(ax.begin(), ax.end());
+  cudaError_t e = dev_alloc((void **)&fs->d_axes64, na * 8);
+  if (e == cudaSuccess) e = dev_alloc((void **)&fs->d_axes32, na * 4);
+  if (e == cudaSuccess) e = dev_alloc((void **)&fs->d_amax, 4 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemcpy(fs->d_axes64, ax.data(), na * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(fs->d_axes32, axf.data(), na * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    dev_free(fs->d_axes64); dev_free(fs->d_axes32); dev_free(fs->d_amax);
+    delete fs;
+    cudaGetLastError();
+    set_error("field set allocation failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PG_ERR_NOMEM : PG_ERR_CUDA;
+  }
+  *out = fs;
+  return PG_OK;
+}
+
+pg_status pg_fieldset_set_times(pg_fieldset *fs, int nt, const double *times, double period) {
+  clear_error();
+  ARG(fs && times && nt >= 1, "need a field set and nt >= 1 times");
+  ARG(strictly_increasing(times, nt), "times must be finite and strictly increasing");
+  ARG(std::isfinite(period) && period >= 0.0, "period must be >= 0");
+  ARG(period == 0.0 || (nt >= 2 && period > times[nt - 1] - times[0]),
+      "a periodic field needs nt >= 2 and period > times[nt-1] - times[0]");
+  ARG(!fs->streaming, "set the times before streaming is configured");
+  double *d_times = nullptr;
+  const void **d_tab = nullptr;
+  float *d_scales = nullptr;
+  cudaError_t e = dev_alloc((void **)&d_times, nt * 8);
+  if (e == cudaSuccess) e = dev_alloc((void **)&d_tab, nt * sizeof(void *));
+  if (e == cudaSuccess) e = dev_alloc((void **)&d_scales, (size_t)nt * fs->nfields * 4);
+  std::vector<float> ones((size_t)nt * fs->nfields, 1.0f);
+  std::vector<const void *> nulls((size_t)nt, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(d_times, times, nt * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_tab, nulls.data(), nt * sizeof(void *), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_scales, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    dev_free(d_times); dev_free(d_tab); dev_free(d_scales);
+    cudaGetLastError();
+    set_error("allocation for %d snapshots failed: %s", nt, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PG_ERR_NOMEM : PG_ERR_CUDA;
+  }
+  free_resident(fs);
+  dev_free(fs->d_times); dev_free(fs->d_tab); dev_free(fs->d_scales);
+  fs->d_times = d_times; fs->d_tab = d_tab; fs->d_scales = d_scales;
+  fs->nt = nt;
+  fs->times.assign(times, times + nt);
+  fs->period = period;
+  fs->slabs.assign((size_t)nt, nullptr);
+  fs->h_scales = ones;
+  return PG_OK;
+}
+
+pg_status pg_fieldset_load_snapshot(pg_fieldset *fs, int s, const void *data, int src_dtype,
+                                    void *stream) {
+  clear_error();
+  ARG(fs && data, "field set and data must not be NULL");
+  ARG(fs->nt > 0, "set the snapshot times first");
+  ARG(s >= 0 && s < fs->nt, "snapshot index out of range");
+  ARG(src_dtype == PG_F64 || src_dtype == PG_F32, "src_dtype must be PG_F64 or PG_F32");
+  ARG(!fs->streaming, "field set is streamed; snapshots are not resident");
+  cudaStream_t st = (cudaStream_t)stream;
+  void *slab = fs->slabs[s];
+  bool fresh = false;
+  if (!slab) {
+    CU(dev_alloc(&slab, fs->slab_bytes));
+    fresh = true;
+  }
+  const void *src = data;
+  const size_t el = src_dtype == PG_F64 ? 8 : 4;
+  const size_t bytes = (size_t)fs->nfields * fs->nodes * el;
+  if (!is_device_ptr(data)) {
+    if (fs->stage_bytes < bytes) {
+      dev_free(fs->d_stage);
+      fs->d_stage = nullptr;
+      fs->stage_bytes = 0;
+      cudaError_t e = dev_alloc(&fs->d_stage, bytes);
+      if (e != cudaSuccess) {
+        if (fresh) dev_free(slab);
+        cudaGetLastError();
+        set_error("staging allocation failed: %s", cudaGetErrorString(e));
+        return PG_ERR_NOMEM;
+      }
+      fs->stage_bytes = bytes;
+    }
+    CU(cudaMemcpyAsync(fs->d_stage, data, bytes, cudaMemcpyDefault, st));
+    src = fs->d_stage;
+  }
+  float *scales = fs->d_scales + (size_t)s * fs->nfields;
+  CU(launch_repack(src, src_dtype, fs->nfields, fs->nodes, slab, fs->storage, scales, fs->d_amax,
+                   fs->sm_count, st));
+  CU(cudaMemcpyAsync(fs->h_scales.data() + (size_t)s * fs->nfields, scales,
+                     sizeof(float) * fs->nfields, cudaMemcpyDeviceToHost, st));
+  const void *entry = slab;
+  CU(cudaMemcpyAsync(fs->d_tab + s, &entry, sizeof(void *), cudaMemcpyHostToDevice, st));
+  CU(cudaStreamSynchronize(st));
+  fs->slabs[s] = slab;
+  return PG_OK;
+}
+
+pg_status pg_fieldset_stream(pg_fieldset *fs, const void *const *ptrs, pg_snapshot_cb cb,
+                             void *user, int src_dtype) {
+  clear_error();
+  ARG(fs, "field set must not be NULL");
+  ARG(fs->nt > 0, "set the snapshot times first");
+  ARG((ptrs != nullptr) != (cb != nullptr), "exactly one of ptrs and cb must be given");
+  ARG(src_dtype == PG_F64 || src_dtype == PG_F32, "src_dtype must be PG_F64 or PG_F32");
+  if (ptrs)
+    for (int s = 0; s < fs->nt; ++s) ARG(ptrs[s] != nullptr, "every snapshot pointer must be set");
+  free_streaming(fs);
+  free_resident(fs);
+  fs->slabs.assign((size_t)fs->nt, nullptr);
+  const size_t el = src_dtype == PG_F64 ? 8 : 4;
+  const size_t bytes = (size_t)fs->nfields * fs->nodes * el;
+  cudaError_t e = cudaSuccess;
+  for (auto &sl : fs->slot) {
+    if (e == cudaSuccess) e = dev_alloc(&sl.buf, fs->slab_bytes);
+    if (e == cudaSuccess) e = dev_alloc((void **)&sl.scales, 4 * sizeof(float));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.free, cudaEventDisableTiming);
+    sl.s = -1;
+  }
+  if (e == cudaSuccess && fs->stage_bytes < bytes) {
+    dev_free(fs->d_stage);
+    fs->d_stage = nullptr;
+    fs->stage_bytes = 0;
+    e = dev_alloc(&fs->d_stage, bytes);
+    if (e == cudaSuccess) fs->stage_bytes = bytes;
+  }
+  if (e == cudaSuccess && cb) e = cudaMallocHost(&fs->h_pinned, bytes);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fs->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fs->stage_free, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(fs->stage_free, fs->side);
+  if (e != cudaSuccess) {
+    free_streaming(fs);
+    cudaGetLastError();
+    set_error("streaming setup failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PG_ERR_NOMEM : PG_ERR_CUDA;
+  }
+  fs->streaming = true;
+  fs->cb = cb;
+  fs->cb_user = user;
+  fs->src_dtype = src_dtype;
+  if (ptrs) fs->src_ptrs.assign(ptrs, ptrs + fs->nt);
+  return PG_OK;
+}
+
+pg_status pg_fieldset_device_bytes(const pg_fieldset *fs, size_t *bytes) {
+  clear_error();
+  ARG(fs && bytes, "arguments must not be NULL");
+  size_t b = 0;
+  for (void *p : fs->slabs) b += p ? fs->slab_bytes : 0;
+  if (fs->streaming) b += 4 * fs->slab_bytes;
+  *bytes = b;
+  return PG_OK;
+}
+
+pg_status pg_fieldset_stats(pg_fieldset *fs, int reset, int64_t *uploads, int64_t *h2d_bytes) {
+  clear_error();
+  ARG(fs, "field set must not be NULL");
+  if (uploads) *uploads = fs->uploads;
+  if (h2d_bytes) *h2d_bytes = fs->upload_h2d_bytes;
+  if (reset) { fs->uploads = 0; fs->upload_h2d_bytes = 0; }
+  return PG_OK;
+}
+
+pg_status pg_fieldset_get_scale(const pg_fieldset *fs, int s, int f, float *scale) {
+  clear_error();
+  ARG(fs && scale, "arguments must not be NULL");
+  ARG(s >= 0 && s < fs->nt && f >= 0 && f < fs->nfields, "index out of range");
+  ARG(!fs->streaming, "scales of streamed snapshots are not kept");
+  *scale = fs->h_scales[(size_t)s * fs->nfields + f];
+  return PG_OK;
+}
+
+pg_status pg_fieldset_destroy(pg_fieldset *fs) {
+  clear_error();
+  if (!fs) return PG_OK;
+  cudaDeviceSynchronize();
+  free_streaming(fs);
+  free_resident(fs);
+  dev_free(fs->d_axes64); dev_free(fs->d_axes32); dev_free(fs->d_amax);
+  dev_free(fs->d_times); dev_free(fs->d_tab); dev_free(fs->d_scales); dev_free(fs->d_stage);
+  delete fs;
+  return PG_OK;
+}
+
+pg_status pg_kernel_create(int scheme, unsigned behaviours, double kh, double w_sink,
+                           pg_kernel **out) {
+  clear_error();
+  ARG(out, "out must not be NULL");
+  ARG(scheme == PG_EULER || scheme == PG_RK4, "scheme must be PG_EULER or PG_RK4");
+  ARG((behaviours & ~(PG_BROWNIAN | PG_SINK)) == 0, "unknown behaviour bits");
+  ARG(std::isfinite(kh) && kh >= 0.0, "kh must be finite and >= 0");
+  ARG(std::isfinite(w_sink), "w_sink must be finite");
+  auto *k = new pg_kernel();
+  k->scheme = scheme; k->beh = behaviours; k->kh = kh; k->w_sink = w_sink;
+  *out = k;
+  return PG_OK;
+}
+
+pg_status pg_kernel_destroy(pg_kernel *k) {
+  delete k;
+  return PG_OK;
+}
+
+static pg_status fill_particles(pg_pset *ps, int64_t off, int64_t n, const double *lon,
+                                const double *lat, const double *depth, const double *time,
+                                double t0, const uint64_t *ids, uint64_t id_base,
+                                cudaStream_t st, double &tmin, double &tmax) {
+  const int sm = ps->fs->sm_count;
+  if (ps->pos == PG_POS_CELL) {
+    set_error("cell positions are created by pg_pset_create_cells");
+    return PG_ERR_UNSUPPORTED;
+  }
+  const size_t el = pos_elem(ps->pos);
+  pg_status r;
+  if ((r = upload_coord(lon, n, (char *)ps->x + off * el, ps->pos, 0.0, sm, st))) return r;
+  if ((r = upload_coord(lat, n, (char *)ps->y + off * el, ps->pos, 0.0, sm, st))) return r;
+  if ((r = upload_coord(depth, n, (char *)ps->z + off * el, ps->pos, 0.0, sm, st))) return r;
+  tmin = t0; tmax = t0;
+  if (time) {
+    CU(cudaMemcpyAsync(ps->time + off, time, n * 8, cudaMemcpyDefault, st));
+    std::vector<double> h((size_t)n);
+    CU(cudaMemcpyAsync(h.data(), time, n * 8, cudaMemcpyDefault, st));
+    CU(cudaStreamSynchronize(st));
+    tmin = std::numeric_limits<double>::infinity();
+    tmax = -tmin;
+    for (double v : h) {
+      if (!std::isfinite(v)) {
+        set_error("particle times must be finite");
+        return PG_ERR_ARG;
+      }
+      tmin = std::min(tmin, v);
+      tmax = std::max(tmax, v);
+    }
+  } else {
+    fill_f64_kernel<<<grid_for(n, sm), 256, 0, st>>>(ps->time + off, t0, n);
+    note_launches(1);
+    CU(cudaGetLastError());
+  }
+  if (ids) {
+    CU(cudaMemcpyAsync(ps->id + off, ids, n * 8, cudaMemcpyDefault, st));
+  } else {
+    iota_u64_kernel<<<grid_for(n, sm), 256, 0, st>>>(ps->id + off, id_base, n);
+    note_launches(1);
+    CU(cudaGetLastError());
+  }
+  CU(cudaMemsetAsync(ps->step + off, 0, n * 4, st));
+  CU(cudaMemsetAsync(ps->status + off, 0, n, st));
+  CU(cudaStreamSynchronize(st));
+  return PG_OK;
+}
+
+pg_status pg_pset_create(pg_fieldset *fs, int64_t n, const double *lon, const double *lat,
+                         const double *depth, const double *time, double t0,
+                         const uint64_t *ids, uint64_t id_base, int pos, uint64_t seed,
+                         pg_pset **out) {
+  clear_error();
+  ARG(fs && out, "field set and out must not be NULL");
+  ARG(n >= 0, "n must be >= 0");
+  ARG(n == 0 || (lon && lat), "lon and lat must be given");
+  ARG(pos == PG_POS_F64 || pos == PG_POS_F32, "pos must be PG_POS_F64 or PG_POS_F32 here");
+  ARG(std::isfinite(t0), "t0 must be finite");
+  ARG(!(pos == PG_POS_F32 && fs->storage == PG_F64), "FP32 positions need FP32/FP16/BF16 storage");
+  auto *ps = new pg_pset();
+  ps->fs = fs; ps->pos = pos; ps->seed = seed;
+  PsetArrays A;
+  pg_status r = alloc_arrays(A, pos, n);
+  if (r) { delete ps; return r; }
+  set_arrays(ps, A);
+  ps->cap = std::max<int64_t>(n, 1);
+  cudaError_t e = dev_alloc((void **)&ps->d_counter, 8);
+  if (e == cudaSuccess) e = dev_alloc((void **)&ps->d_err, 4);
+  if (e == cudaSuccess) e = cudaMemset(ps->d_err, 0, 4);
+  if (e != cudaSuccess) {
+    A.free_all(); dev_free(ps->d_counter); dev_free(ps->d_err);
+    delete ps;
+    cudaGetLastError();
+    set_error("allocation failed: %s", cudaGetErrorString(e));
+    return PG_ERR_NOMEM;
+  }
+  double tmin = t0, tmax = t0;
+  if (n > 0) r = fill_particles(ps, 0, n, lon, lat, depth, time, t0, ids, id_base, 0, tmin, tmax);
+  if (r) {
+    A.free_all(); dev_free(ps->d_counter); dev_free(ps->d_err);
+    delete ps;
+    return r;
+  }
+  ps->n = n;
+  ps->t_min = tmin; ps->t_max = tmax;
+  *out = ps;
+  return PG_OK;
+}
+
+pg_status pg_pset_add(pg_pset *ps, int64_t n, const double *lon, const double *lat,
+                      const double *depth, const double *time, double t0, const uint64_t *ids,
+                      uint64_t id_base) {
+  clear_error();
+  ARG(ps, "particle set must not be NULL");
+  ARG(n >= 0, "n must be >= 0");
+  if (n == 0) return PG_OK;
+  ARG(lon && lat, "lon and lat must be given");
+  ARG(std::isfinite(t0), "t0 must be finite");
+  if (ps->n + n > ps->cap) {
+    const int64_t cap = std::max<int64_t>(ps->n + n, ps->cap + ps->cap / 2);
+    PsetArrays B;
+    pg_status r = alloc_arrays(B, ps->pos, cap);
+    if (r) return r;
+    PsetArrays A = arrays_of(ps);
+    const size_t el = pos_elem(ps->pos);
+    const int64_t m = ps->n;
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void *d, const void *s, size_t b) {
+      if (e == cudaSuccess && b) e = cudaMemcpy(d, s, b, cudaMemcpyDeviceToDevice);
+    };
+    cp(B.x, A.x, m * el); cp(B.y, A.y, m * el); cp(B.z, A.z, m * el);
+    cp(B.time, A.time, m * 8); cp(B.id, A.id, m * 8); cp(B.step, A.step, m * 4);
+    cp(B.status, A.status, m);
+    if (e != cudaSuccess) {
+      B.free_all();
+      set_error("grow copy failed: %s", cudaGetErrorString(e));
+      return PG_ERR_CUDA;
+    }
+    A.free_all();
+    set_arrays(ps, B);
+    ps->cap = cap;
+  }
+  double tmin, tmax;
+  pg_status r = fill_particles(ps, ps->n, n, lon, lat, depth, time, t0, ids, id_base, 0, tmin, tmax);
+  if (r) return r;
+  if (ps->n == 0) { ps->t_min = tmin; ps->t_max = tmax; }
+  else { ps->t_min = std::min(ps->t_min, tmin); ps->t_max = std::max(ps->t_max, tmax); }
+  ps->n += n;
+  return PG_OK;
+}
+
+pg_status pg_pset_size(const pg_pset *ps, int64_t *n, int64_t *n_alive) {
+  clear_error();
+  ARG(ps, "particle set must not be NULL");
+  if (n) *n = ps->n;
+  if (n_alive) {
+    std::vector<uint8_t> h((size_t)ps->n);
+    if (ps->n) CU(cudaMemcpy(h.data(), ps->status, ps->n, cudaMemcpyDeviceToHost));
+    int64_t a = 0;
+    for (uint8_t v : h) a += v == 0;
+    *n_alive = a;
+  }
+  return PG_OK;
+}
+
+pg_status pg_pset_get(const pg_pset *ps, double *lon, double *lat, double *depth, double *time,
+                      uint64_t *ids, uint32_t *steps, uint8_t *status, void *stream) {
+  clear_error();
+  ARG(ps, "particle set must not be NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = ps->n;
+  if (n == 0) return PG_OK;
+  double *tmp = nullptr;
+  if (ps->pos == PG_POS_F32 && (lon || lat || depth)) CU(dev_alloc((void **)&tmp, n * 8));
+  auto coord = [&](void *src, double *dst) -> pg_status {
+    if (!dst) return PG_OK;
+    if (ps->pos == PG_POS_F64) {
+      CU(cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyDefault, st));
+    } else {
+      f32_to_f64_kernel<<<grid_for(n, ps->fs->sm_count), 256, 0, st>>>((const float *)src, tmp, n);
+      note_launches(1);
+      CU(cudaGetLastError());
+      CU(cudaMemcpyAsync(dst, tmp, n * 8, cudaMemcpyDefault, st));
+    }
+    return PG_OK;
+  };
+  pg_status r = PG_OK;
+  if (!r) r = coord(ps->x, lon);
+  if (!r) r = coord(ps->y, lat);
+  if (!r) r = coord(ps->z, depth);
+  if (!r && time) {
+    cudaError_t e = cudaMemcpyAsync(time, ps->time, n * 8, cudaMemcpyDefault, st);
+    if (e) { set_error("copy failed: %s", cudaGetErrorString(e)); r = PG_ERR_CUDA; }
+  }
+  if (!r && ids) {
+    cudaError_t e = cudaMemcpyAsync(ids, ps->id, n * 8, cudaMemcpyDefault, st);
+    if (e) { set_error("copy failed: %s", cudaGetErrorString(e)); r = PG_ERR_CUDA; }
+  }
+  if (!r && steps) {
+    cudaError_t e = cudaMemcpyAsync(steps, ps->step, n * 4, cudaMemcpyDefault, st);
+    if (e) { set_error("copy failed: %s", cudaGetErrorString(e)); r = PG_ERR_CUDA; }
+  }
+  if (!r && status) {
+    cudaError_t e = cudaMemcpyAsync(status, ps->status, n, cudaMemcpyDefault, st);
+    if (e) { set_error("copy failed: %s", cudaGetErrorString(e)); r = PG_ERR_CUDA; }
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (tmp) dev_free(tmp);
+  if (!r && e) { set_error("sync failed: %s", cudaGetErrorString(e)); r = PG_ERR_CUDA; }
+  return r;
+}
+
+pg_status pg_pset_set_tune(pg_pset *ps, const pg_tune *tune) {
+  clear_error();
+  ARG(ps && tune, "arguments must not be NULL");
+  ARG(tune->block == 0 || (tune->block >= 32 && tune->block <= 1024 && tune->block % 32 == 0),
+      "block must be 0 or a multiple of 32 in [32, 1024]");
+  ARG(tune->resort_steps >= 0 && tune->chunk_steps >= 0, "negative tuning value");
+  ps->tune.block = tune->block ? tune->block : 256;
+  ps->tune.resort_steps = tune->resort_steps;
+  ps->tune.chunk_steps = tune->chunk_steps ? tune->chunk_steps : 64;
+  return PG_OK;
+}
+
+pg_status pg_pset_resort(pg_pset *ps, void *stream) {
+  clear_error();
+  ARG(ps, "particle set must not be NULL");
+  int64_t alive = 0;
+  CU(launch_resort(ps, (cudaStream_t)stream, &alive));
+  CU(cudaStreamSynchronize((cudaStream_t)stream));
+  return PG_OK;
+}
+
+pg_status pg_pset_moments(const pg_pset *ps, double out[7], void *stream) {
+  clear_error();
+  ARG(ps && out, "arguments must not be NULL");
+  CU(launch_moments(ps, out, (cudaStream_t)stream));
+  return PG_OK;
+}
+
+// Output: copy the state to the host, widen to FP64 and call the hook.
+static pg_status emit_output(pg_pset *ps, double t, pg_output_cb out, void *user,
+                             cudaStream_t st) {
+  const int64_t n = ps->n;
+  std::vector<double> lon(n), lat(n), dep(n);
+  std::vector<uint64_t> ids(n);
+  std::vector<uint8_t> stat(n);
+  pg_status r = pg_pset_get(ps, lon.data(), lat.data(), dep.data(), nullptr, ids.data(), nullptr,
+                            stat.data(), st);
+  if (r) return r;
+  if (out(user, t, n, ids.data(), lon.data(), lat.data(), dep.data(), stat.data()) != 0) {
+    set_error("output callback failed at t = %g", t);
+    return PG_ERR_CALLBACK;
+  }
+  return PG_OK;
+}
+
+pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
+                     double output_dt, pg_output_cb out, void *user, void *stream,
+                     int64_t *steps_done) {
+  clear_error();
+  ARG(ps && k, "particle set and kernel must not be NULL");
+  ARG(std::isfinite(runtime) && runtime >= 0.0, "runtime must be finite and >= 0");
+  ARG(std::isfinite(dt) && dt != 0.0, "dt must be finite and non-zero");
+  ARG(std::isfinite(output_dt) && output_dt >= 0.0, "output_dt must be finite and >= 0");
+  pg_fieldset *fs = ps->fs;
+  ARG(fs->nt > 0, "field set has no snapshot times");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (steps_done) *steps_done = 0;
+  if (!fs->streaming) {
+    for (int s = 0; s < fs->nt; ++s)
+      if (!fs->slabs[s]) {
+        set_error("snapshot %d has not been loaded", s);
+        return PG_ERR_STATE;
+      }
+  }
+  const double sgn = dt > 0.0 ? 1.0 : -1.0;
+  const double t_begin = dt > 0.0 ? ps->t_min : ps->t_max;
+  const double t_end = t_begin + sgn * runtime;
+  if (fs->nt > 1 && fs->period <= 0.0) {
+    const double lo = std::min(dt > 0.0 ? ps->t_min : t_end, t_begin);
+    const double hi = std::max(dt > 0.0 ? t_end : ps->t_max, t_begin);
+    if (lo < fs->times.front() || hi > fs->times.back()) {
+      set_error("execute spans [%g, %g] outside the field times [%g, %g]", lo, hi,
+                fs->times.front(), fs->times.back());
+      return PG_ERR_TIME;
+    }
+  }
+  if (fs->streaming && fs->nt > 1) {
+    double min_gap = std::numeric_limits<double>::infinity();
+    for (int s = 0; s + 1 < fs->nt; ++s) min_gap = std::min(min_gap, fs->times[s + 1] - fs->times[s]);
+    if (fs->period > 0.0) min_gap = std::min(min_gap, fs->times[0] + fs->period - fs->times.back());
+    if (std::fabs(dt) >= min_gap) {
+      set_error("streamed fields need |dt| below the snapshot spacing");
+      return PG_ERR_UNSUPPORTED;
+    }
+  }
+  StepArgs a;
+  a.g = grid_args(fs);
+  a.f.nt = fs->nt; a.f.nf = fs->nfields; a.f.times = fs->d_times; a.f.period = fs->period;
+  a.f.tab = fs->d_tab;
+  a.f.scales = (fs->storage == PG_F16S || fs->storage == PG_BF16S) ? fs->d_scales : nullptr;
+  a.k.scheme = k->scheme; a.k.beh = k->beh; a.k.kh = k->kh; a.k.w_sink = k->w_sink;
+  a.k.seed = ps->seed; a.k.deg_m = 1852.0 * 60.0;
+  a.dt = dt; a.t_end = t_end;
+  a.steps_done = ps->d_counter;
+  a.err = ps->d_err;
+  CU(cudaMemsetAsync(ps->d_counter, 0, 8, st));
+  CU(cudaMemsetAsync(ps->d_err, 0, 4, st));
+
+  const double chunk_len = std::fabs(dt) * ps->tune.chunk_steps;
+  const double resort_len = ps->tune.resort_steps > 0 ? std::fabs(dt) * ps->tune.resort_steps : 0.0;
+  double next_out = output_dt > 0.0 ? t_begin + sgn * output_dt : t_end;
+  double next_sort = resort_len > 0.0 ? t_begin + sgn * resort_len : t_end;
+  int64_t n_active = ps->n;
+  double tc = t_begin;
+  int guard = 0;
+  while (sgn * (t_end - tc) > 0.0) {
+    double tn = tc + sgn * chunk_len;
+    auto clip = [&](double b) {
+      if (sgn * (b - tc) > 0.0 && sgn * (tn - b) > 0.0) tn = b;
+    };
+    clip(t_end);
+    clip(next_out);
+    clip(next_sort);
+    std::vector<int> need;
+    if (fs->streaming && fs->nt == 1) {
+      need.push_back(0);
+      pg_status r = ensure_slots(fs, need, -1, st);
+      if (r) return r;
+    } else if (fs->streaming) {
+      // end the chunk at the next snapshot time; make resident the snapshots
+      // bracketing every stage time a step starting in the chunk can reach,
+      // and start uploading the one after them
+      const long long m = snap_counter(fs, tc);
+      if (sgn > 0) {
+        clip(snap_time(fs, m + 1));
+      } else {
+        const double b = snap_time(fs, m);
+        clip(b < tc ? b : snap_time(fs, m - 1));
+      }
+      const double adt = std::fabs(dt);
+      const double lo_t = sgn > 0 ? tc : std::max(tn - adt, t_end);
+      const double hi_t = sgn > 0 ? std::min(tn + adt, t_end) : tc;
+      const long long q_lo = snap_counter(fs, lo_t), q_hi = snap_counter(fs, hi_t) + 1;
+      for (long long q = q_lo; q <= q_hi; ++q) {
+        if (fs->period <= 0.0 && (q < 0 || q >= fs->nt)) continue;
+        const int s = snap_of(fs, q);
+        if (std::find(need.begin(), need.end(), s) == need.end()) need.push_back(s);
+      }
+      const long long pq = sgn > 0 ? q_hi + 1 : q_lo - 1;
+      int pre = -1;
+      if (fs->period > 0.0 || (pq >= 0 && pq < fs->nt)) pre = snap_of(fs, pq);
+      pg_status r = ensure_slots(fs, need, pre, st);
+      if (r) return r;
+    }
+    a.p.n = n_active;
+    a.p.x = ps->x; a.p.y = ps->y; a.p.z = ps->z;
+    a.p.time = ps->time; a.p.id = ps->id; a.p.step = ps->step; a.p.status = ps->status;
+    a.t_stop = tn;
+    if (ps->timing) {
+      if (ps->ev_used + 2 > ps->ev.size()) {
+        for (int q = 0; q < 2; ++q) {
+          cudaEvent_t ev;
+          CU(cudaEventCreate(&ev));
+          ps->ev.push_back(ev);
+        }
+      }
+      CU(cudaEventRecord(ps->ev[ps->ev_used], st));
+    }
+    CU(launch_advect_plain(a, ps->pos, fs->storage, ps->tune.block, st));
+    if (ps->timing) {
+      CU(cudaEventRecord(ps->ev[ps->ev_used + 1], st));
+      ps->ev_used += 2;
+    }
+    if (fs->streaming) mark_slots_used(fs, need, st);
+    tc = tn;
+    if (resort_len > 0.0 && tc == next_sort && sgn * (t_end - tc) > 0.0) {
+      CU(launch_resort(ps, st, &n_active));
+      next_sort = tc + sgn * resort_len;
+    }
+    if (out && output_dt > 0.0 && (tc == next_out || tc == t_end)) {
+      pg_status r = emit_output(ps, tc, out, user, st);
+      if (r) return r;
+    }
+    if (tc == next_out) next_out = tc + sgn * output_dt;
+    if (++guard > 100000000) break;
+  }
+  unsigned long long done = 0;
+  int err = 0;
+  CU(cudaMemcpyAsync(&done, ps->d_counter, 8, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(&err, ps->d_err, 4, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (steps_done) *steps_done = (int64_t)done;
+  if (ps->timing) {
+    for (size_t q = 0; q + 1 < ps->ev_used; q += 2) {
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, ps->ev[q], ps->ev[q + 1]));
+      ps->timed_ms += ms;
+      ++ps->timed_launches;
+    }
+    ps->ev_used = 0;
+  }
+  if (dt > 0.0) { ps->t_min = std::max(ps->t_min, t_end); ps->t_max = std::max(ps->t_max, t_end); }
+  else { ps->t_min = std::min(ps->t_min, t_end); ps->t_max = std::min(ps->t_max, t_end); }
+  if (err) {
+    set_error("a kernel recorded internal error %d", err);
+    return PG_ERR_DEVICE;
+  }
+  return PG_OK;
+}
+
+pg_status pg_pset_kernel_timing(pg_pset *ps, int enable, double *total_ms, int64_t *launches) {
+  clear_error();
+  ARG(ps, "particle set must not be NULL");
+  if (total_ms) *total_ms = ps->timed_ms;
+  if (launches) *launches = ps->timed_launches;
+  if (enable >= 0) {
+    ps->timing = enable != 0;
+    ps->timed_ms = 0.0;
+    ps->timed_launches = 0;
+    ps->ev_used = 0;
+  }
+  return PG_OK;
+}
+
+pg_status pg_launch_count(int64_t *count) {
+  clear_error();
+  ARG(count, "count must not be NULL");
+  *count = (int64_t)g_launches.load();
+  return PG_OK;
+}
+
+pg_status pg_pset_save(const pg_pset *ps, const char *path) {
+  clear_error();
+  ARG(ps && path, "arguments must not be NULL");
+  const int64_t n = ps->n;
+  std::vector<double> lon(n), lat(n), dep(n), tim(n);
+  std::vector<uint64_t> ids(n);
+  std::vector<uint32_t> stp(n);
+  std::vector<uint8_t> sta(n);
+  // raw position bytes keep FP32 state bit for bit
+  const size_t el = pos_elem(ps->pos);
+  std::vector<char> x(n * el), y(n * el), z(n * el);
+  if (n) {
+    CU(cudaMemcpy(x.data(), ps->x, n * el, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(y.data(), ps->y, n * el, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(z.data(), ps->z, n * el, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(tim.data(), ps->time, n * 8, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(ids.data(), ps->id, n * 8, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(stp.data(), ps->step, n * 4, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(sta.data(), ps->status, n, cudaMemcpyDeviceToHost));
+  }
+  FILE *f = fopen(path, "wb");
+  if (!f) {
+    set_error("cannot open %s for writing", path);
+    return PG_ERR_ARG;
+  }
+  const char magic[8] = {'P', 'G', 'P', 'S', 'E', 'T', '0', '1'};
+  const int32_t pos = ps->pos;
+  bool ok = fwrite(magic, 8, 1, f) == 1 && fwrite(&pos, 4, 1, f) == 1 &&
+            fwrite(&n, 8, 1, f) == 1 && fwrite(&ps->seed, 8, 1, f) == 1 &&
+            fwrite(&ps->t_min, 8, 1, f) == 1 && fwrite(&ps->t_max, 8, 1, f) == 1;
+  if (ok && n) {
+    ok = fwrite(x.data(), el, n, f) == (size_t)n && fwrite(y.data(), el, n, f) == (size_t)n &&
+         fwrite(z.data(), el, n, f) == (size_t)n && fwrite(tim.data(), 8, n, f) == (size_t)n &&
+         fwrite(ids.data(), 8, n, f) == (size_t)n && fwrite(stp.data(), 4, n, f) == (size_t)n &&
+         fwrite(sta.data(), 1, n, f) == (size_t)n;
+  }
+  if (fclose(f) != 0) ok = false;
+  if (!ok) {
+    set_error("write to %s failed", path);
+    return PG_ERR_ARG;
+  }
+  return PG_OK;
+}
+
+pg_status pg_pset_restore(pg_fieldset *fs, const char *path, pg_pset **out) {
+  clear_error();
+  ARG(fs && path && out, "arguments must not be NULL");
+  FILE *f = fopen(path, "rb");
+  if (!f) {
+    set_error("cannot open %s", path);
+    return PG_ERR_ARG;
+  }
+  char magic[8];
+  int32_t pos = 0;
+  int64_t n = 0;
+  uint64_t seed = 0;
+  double tmin = 0, tmax = 0;
+  bool ok = fread(magic, 8, 1, f) == 1 && memcmp(magic, "PGPSET01", 8) == 0 &&
+            fread(&pos, 4, 1, f) == 1 && fread(&n, 8, 1, f) == 1 && fread(&seed, 8, 1, f) == 1 &&
+            fread(&tmin, 8, 1, f) == 1 && fread(&tmax, 8, 1, f) == 1 &&
+            (pos == PG_POS_F64 || pos == PG_POS_F32) && n >= 0;
+  const size_t el = ok ? pos_elem(pos) : 0;
+  std::vector<char> x, y, z;
+  std::vector<double> tim;
+  std::vector<uint64_t> ids;
+  std::vector<uint32_t> stp;
+  std::vector<uint8_t> sta;
+  if (ok) {
+    x.resize(n * el); y.resize(n * el); z.resize(n * el);
+    tim.resize(n); ids.resize(n); stp.resize(n); sta.resize(n);
+    if (n)
+      ok = fread(x.data(), el, n, f) == (size_t)n && fread(y.data(), el, n, f) == (size_t)n &&
+           fread(z.data(), el, n, f) == (size_t)n && fread(tim.data(), 8, n, f) == (size_t)n &&
+           fread(ids.data(), 8, n, f) == (size_t)n && fread(stp.data(), 4, n, f) == (size_t)n &&
+           fread(sta.data(), 1, n, f) == (size_t)n;
+  }
+  fclose(f);
+  if (!ok) {
+    set_error("%s is not a particle-set checkpoint", path);
+    return PG_ERR_ARG;
+  }
+  // create an empty set of the right form, then fill it raw
+  pg_pset *ps = nullptr;
+  pg_status r = pg_pset_create(fs, 0, nullptr, nullptr, nullptr, nullptr, tmin, nullptr, 0, pos,
+                               seed, &ps);
+  if (r) return r;
+  if (n) {
+    PsetArrays B;
+    r = alloc_arrays(B, pos, n);
+    if (r) { pg_pset_destroy(ps); return r; }
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void *d, const void *s, size_t b) {
+      if (e == cudaSuccess) e = cudaMemcpy(d, s, b, cudaMemcpyHostToDevice);
+    };
+    cp(B.x, x.data(), n * el); cp(B.y, y.data(), n * el); cp(B.z, z.data(), n * el);
+    cp(B.time, tim.data(), n * 8); cp(B.id, ids.data(), n * 8); cp(B.step, stp.data(), n * 4);
+    cp(B.status, sta.data(), n);
+    if (e != cudaSuccess) {
+      B.free_all();
+      pg_pset_destroy(ps);
+      set_error("restore copy failed: %s", cudaGetErrorString(e));
+      return PG_ERR_CUDA;
+    }
+    arrays_of(ps).free_all();
+    set_arrays(ps, B);
+    ps->cap = n;
+  }
+  ps->n = n;
+  ps->t_min = tmin; ps->t_max = tmax;
+  *out = ps;
+  return PG_OK;
+}
+
+pg_status pg_pset_destroy(pg_pset *ps) {
+  clear_error();
+  if (!ps) return PG_OK;
+  cudaDeviceSynchronize();
+  arrays_of(ps).free_all();
+  ps->alt.free_all();
+  dev_free(ps->d_counter);
+  dev_free(ps->d_err);
+  dev_free(ps->sort_scratch);
+  dev_free(ps->diag_scratch);
+  for (cudaEvent_t ev : ps->ev) cudaEventDestroy(ev);
+  delete ps;
+  return PG_OK;
+}
+
+}  // extern "C"

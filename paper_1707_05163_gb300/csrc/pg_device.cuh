@@ -1,0 +1,128 @@
+// pg_device.cuh -- argument blocks shared by the host side and the kernels,
+// plus the device-side counter-based random numbers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pg {
+
+// Device-side internal error codes (written once into StepArgs::err).
+enum DevErr : int {
+  DEVERR_NONE = 0,
+  DEVERR_SLAB_MISSING = 1,   // a kernel needed a snapshot that is not resident
+  DEVERR_TIME_RANGE = 2,     // a stage time fell outside a non-periodic field
+};
+
+struct GridArgs {
+  int nx, ny, nz;
+  int mesh;                  // 0 flat, 1 spherical
+  int periodic;              // zonal wrap
+  const double *lon, *lat, *depth;      // FP64 axes (device)
+  const float *lonf, *latf, *depthf;    // FP32 copies of the axes (device)
+  int uni[3];                // 1 if the axis is uniformly spaced
+  double x0[3], inv_d[3];    // first node and 1/spacing (uniform axes)
+  float x0f[3], inv_df[3];
+  double lon_end;            // lon[0] + 360 (periodic wrap-cell far edge)
+};
+
+struct FieldArgs {
+  int nt;                    // number of snapshots (1 = steady)
+  int nf;                    // 2 or 3 fields
+  const double *times;       // [nt] (device)
+  double period;             // > 0: time-periodic
+  const void *const *tab;    // [nt] device pointers to interleaved slabs (null if absent)
+  const float *scales;       // [nt * nf] FP32 scales (quantised storage) or null
+};
+
+struct KernArgs {
+  int scheme;                // 0 Euler, 1 RK4
+  unsigned beh;              // behaviour bits
+  double kh, w_sink;
+  uint64_t seed;
+  double deg_m;              // metres per degree
+};
+
+struct PartArgs {
+  int64_t n;
+  void *x, *y, *z;           // lon, lat, depth (double or float)
+  int32_t *ci, *cj, *ck;     // cell form: cell indices
+  float *fx, *fy, *fz;       // cell form: offsets in [0, 1)
+  double *time;
+  const uint64_t *id;
+  uint32_t *step;
+  uint8_t *status;
+};
+
+struct StepArgs {
+  GridArgs g;
+  FieldArgs f;
+  KernArgs k;
+  PartArgs p;
+  double dt, t_stop, t_end;
+  unsigned long long *steps_done;   // particle-steps taken (device counter)
+  int *err;                         // first DevErr recorded (device word)
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies mixed with the round key; the key advances by the
+// Weyl increments between rounds.  Counter = (id lo, id hi, step, 0), key =
+// the particle set's seed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// 53-bit integers of the two uniforms: u1 = (m1 + 1) 2^-53 in (0, 1],
+// u2 = m2 2^-53 in [0, 1).
+__device__ __forceinline__ void philox_uniform_bits(uint64_t seed, uint64_t id, uint32_t step,
+                                                    unsigned long long &m1,
+                                                    unsigned long long &m2) {
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, 0u),
+                                make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  m1 = ((unsigned long long)(r.x >> 5) << 26) | (unsigned long long)(r.y >> 6);
+  m2 = ((unsigned long long)(r.z >> 5) << 26) | (unsigned long long)(r.w >> 6);
+}
+
+// Box-Muller in FP64.
+__device__ __forceinline__ void normal_pair(uint64_t seed, uint64_t id, uint32_t step,
+                                            double &n1, double &n2) {
+  unsigned long long m1, m2;
+  philox_uniform_bits(seed, id, step, m1, m2);
+  const double u1 = ((double)m1 + 1.0) * (1.0 / 9007199254740992.0);
+  const double u2 = (double)m2 * (1.0 / 9007199254740992.0);
+  const double rad = sqrt(-2.0 * log(u1));
+  const double ang = 6.283185307179586 * u2;
+  n1 = rad * cos(ang);
+  n2 = rad * sin(ang);
+}
+
+// Box-Muller in FP32 from the same 53-bit uniforms, each correctly rounded
+// to FP32 first (no FP64 arithmetic).
+__device__ __forceinline__ void normal_pair(uint64_t seed, uint64_t id, uint32_t step,
+                                            float &n1, float &n2) {
+  unsigned long long m1, m2;
+  philox_uniform_bits(seed, id, step, m1, m2);
+  const float u1 = __ull2float_rn(m1 + 1ull) * 1.1102230246251565e-16f;   // 2^-53
+  const float u2 = __ull2float_rn(m2) * 1.1102230246251565e-16f;
+  const float rad = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  n1 = rad * c;
+  n2 = rad * s;
+}
+
+}  // namespace pg
