@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--particles", type=int, default=10_000_000)
     ap.add_argument("--days", type=float, default=30.0)
+    ap.add_argument("--snapshots", type=int, default=30,
+                    help="daily snapshots in the periodic field (30 = the workload)")
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--resort-steps", type=int, default=0)
     ap.add_argument("--chunk-steps", type=int, default=48)
@@ -197,7 +199,8 @@ def main():
     import synth
     pg.load()
 
-    gf = synth.GlobalField(res_deg=0.25, nz=50, nt=30, seed=2)
+    gf = synth.GlobalField(res_deg=0.25, nz=50, nt=args.snapshots, seed=2,
+                           period=args.snapshots * DAY)
     bases = make_field_host_bases(gf)
     want_host = (not args.no_e2e) or (rank == 0 and world == 1 and not args.no_cpu)
     host_field = None
