@@ -46,8 +46,8 @@ def parse():
     ap.add_argument("--days", type=float, default=30.0)
     ap.add_argument("--snapshots", type=int, default=30,
                     help="daily snapshots in the periodic field (30 = the workload)")
-    ap.add_argument("--block", type=int, default=256)
-    ap.add_argument("--resort-steps", type=int, default=0)
+    ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--resort-steps", type=int, default=96)
     ap.add_argument("--chunk-steps", type=int, default=48)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

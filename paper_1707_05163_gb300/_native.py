@@ -96,7 +96,7 @@ def load(build_if_missing: bool = True):
         if _lib is not None:
             return _lib
         path = _build.LIB
-        if not os.path.exists(path):
+        if not os.path.exists(path) or os.environ.get("PG_BUILD_DIR"):
             if not build_if_missing:
                 raise ImportError(f"CUDA library not built: {path}")
             _build.build()

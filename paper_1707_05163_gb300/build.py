@@ -12,7 +12,9 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-OUT_DIR = os.path.join(HERE, "_build")
+# PG_BUILD_DIR / PG_MAXRREG: build elsewhere / cap registers of the FP32
+# advection unit (tuning experiments); defaults build the library in-tree.
+OUT_DIR = os.environ.get("PG_BUILD_DIR", os.path.join(HERE, "_build"))
 LIB = os.path.join(OUT_DIR, "libparcels_gb.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
@@ -24,7 +26,8 @@ UNITS = {
     "field_store.cu": [],
     "sort.cu": [],
     "advect_f64.cu": ["-fmad=false"],
-    "advect_f32.cu": [],
+    "advect_f32.cu": ([f"-maxrregcount={os.environ['PG_MAXRREG']}"]
+                      if os.environ.get("PG_MAXRREG") else []),
 }
 
 

@@ -9,14 +9,11 @@ cudaError_t launch_advect_f64(const StepArgs &a, int storage, int block, cudaStr
 
 template <typename Store>
 static cudaError_t launch_f32(const StepArgs &a, int block, cudaStream_t st) {
-  const int64_t grid = (a.p.n + block - 1) / block;
-  if (grid == 0) return cudaSuccess;
+  if (a.p.n == 0) return cudaSuccess;
   const bool d3 = a.g.nz > 1;
-  if (a.f.nf == 3) advect_plain_kernel<float, Store, 3, true><<<(unsigned)grid, block, 0, st>>>(a);
-  else if (d3) advect_plain_kernel<float, Store, 2, true><<<(unsigned)grid, block, 0, st>>>(a);
-  else advect_plain_kernel<float, Store, 2, false><<<(unsigned)grid, block, 0, st>>>(a);
-  note_launches(1);
-  return cudaGetLastError();
+  if (a.f.nf == 3) return launch_clamped(advect_plain_kernel<float, Store, 3, true>, a, block, st);
+  if (d3) return launch_clamped(advect_plain_kernel<float, Store, 2, true>, a, block, st);
+  return launch_clamped(advect_plain_kernel<float, Store, 2, false>, a, block, st);
 }
 
 cudaError_t launch_advect_plain(const StepArgs &a, int real, int storage, int block,

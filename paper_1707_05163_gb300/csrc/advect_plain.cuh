@@ -5,16 +5,19 @@
 // at the corners of the particle's current cell for the two bracketing
 // snapshots.  A stage re-reads the field only when the particle has moved to
 // another cell or another pair of snapshots, so the four RK4 stages of a step
-// and consecutive steps inside one cell share one gather.  The values used
-// are the same ones a fresh gather would return, so the arithmetic is that of
-// the definition.
+// and consecutive steps inside one cell share one gather; when the pair of
+// snapshots advances by one, the shared snapshot's corners are kept and only
+// the new one is read.  The values used are the ones a fresh gather would
+// return, so the arithmetic is that of the definition.
 //
 // Instantiated twice:
 //   Real = double  (compiled with -fmad=false): the FP64 path, which carries
 //     out the oracle's operations in the oracle's order, including the FP64
-//     time interpolation of every stage;
+//     time interpolation of every stage and its cell and interval tie-breaks;
 //   Real = float: the FP32 path, where stage times are FP32 offsets inside
-//     the cached snapshot interval and no FP64 arithmetic runs per stage.
+//     the cached snapshot interval, cell and interval bounds are inclusive on
+//     both sides (continuity makes the two choices at a shared node equal),
+//     and no FP64 arithmetic runs per stage.
 #pragma once
 
 #include "pg_device.cuh"
@@ -24,8 +27,6 @@ namespace pg {
 // ------------------------------------------------------------ node loads ---
 // Interleaved storage: node (k, j, i) holds its NF field values contiguously
 // (NF = 3 padded to 4), so one vector load fetches U, V[, W] of a corner.
-template <int NF> struct NodeStride { static constexpr int value = NF == 2 ? 2 : 4; };
-
 template <typename Real, int NF>
 __device__ __forceinline__ void load_node(const double *p, size_t node, const float *, Real (&v)[NF]) {
   if constexpr (NF == 2) {
@@ -79,8 +80,6 @@ __device__ __forceinline__ void load_node(const __nv_bfloat16 *p, size_t node, c
 }
 
 // ------------------------------------------------------- math per Real ---
-__device__ __forceinline__ double pg_fmod(double a, double b) { return fmod(a, b); }
-__device__ __forceinline__ float pg_fmod(float a, float b) { return fmodf(a, b); }
 __device__ __forceinline__ double pg_floor(double a) { return floor(a); }
 __device__ __forceinline__ float pg_floor(float a) { return floorf(a); }
 __device__ __forceinline__ double pg_sqrt(double a) { return sqrt(a); }
@@ -93,6 +92,16 @@ __device__ __forceinline__ double cos_deg(double lat) {
   return cos(lat * deg2rad);
 }
 __device__ __forceinline__ float cos_deg(float lat) { return cospif(lat * (1.0f / 180.0f)); }
+
+// u (m/s) -> degrees/s of longitude at latitude lat; v (m/s) -> degrees/s.
+__device__ __forceinline__ double lon_rate(double u, double lat, const KernArgs &k) {
+  return u / (k.deg_m * cos_deg(lat));
+}
+__device__ __forceinline__ float lon_rate(float u, float lat, const KernArgs &k) {
+  return __fdividef(u, k.deg_m_f * cos_deg(lat));
+}
+__device__ __forceinline__ double lat_rate(double v, const KernArgs &k) { return v / k.deg_m; }
+__device__ __forceinline__ float lat_rate(float v, const KernArgs &k) { return v * k.inv_deg_m_f; }
 
 template <typename Real> __device__ __forceinline__ const Real *axis(const GridArgs &g, int a);
 template <> __device__ __forceinline__ const double *axis<double>(const GridArgs &g, int a) {
@@ -107,6 +116,8 @@ template <> __device__ __forceinline__ float axis_x0<float>(const GridArgs &g, i
 template <typename Real> __device__ __forceinline__ Real axis_inv(const GridArgs &g, int a);
 template <> __device__ __forceinline__ double axis_inv<double>(const GridArgs &g, int a) { return g.inv_d[a]; }
 template <> __device__ __forceinline__ float axis_inv<float>(const GridArgs &g, int a) { return g.inv_df[a]; }
+__device__ __forceinline__ double lon_end(const GridArgs &g, double) { return g.lon_end; }
+__device__ __forceinline__ float lon_end(const GridArgs &g, float) { return g.lon_end_f; }
 
 // Full search on one axis: the largest i <= n-2 with x[i] <= p, given that
 // x[0] <= p <= x[n-1].  Uniform axes start from floor((p - x0) / dx) and
@@ -142,14 +153,44 @@ struct Sampler {
   // cached snapshot interval and the snapshots whose corners are held
   int s0, s1;
   int gi, gj, gk, gs0, gs1;   // what `v` currently holds (gi = -1: nothing)
-  double ta, tb;              // interval bounds, FP64 path: wrapped; FP32 path: ta unwrapped
+  double ta;                  // FP32 path: interval start in unwrapped time
   float span, rspan;          // FP32 path
   Real v[2][NF][NC];
 
   __device__ __forceinline__ void reset() {
-    ci = -1; cj = -1; ck = -1; s0 = -1; gi = -1;
+    ci = -1; cj = -1; ck = -1; s0 = -1; s1 = -1; gi = -1;
   }
 };
+
+// Reduce a longitude into [x0, x0 + 360).  FP64: the definition's fmod.
+// FP32: stage positions are at most one turn away, so a compare and one
+// add/subtract do (fmod for anything farther).
+__device__ __forceinline__ double wrap_lon(double p, double x0) {
+  double r = fmod(p - x0, 360.0);
+  if (r < 0.0) r += 360.0;
+  if (r >= 360.0) r -= 360.0;
+  return x0 + r;
+}
+__device__ __forceinline__ float wrap_lon(float p, float x0) {
+  float q = p;
+  if (q < x0) q += 360.0f;
+  else if (q >= x0 + 360.0f) q -= 360.0f;
+  if (!(q >= x0 && q < x0 + 360.0f)) {
+    float r = fmodf(p - x0, 360.0f);
+    if (r < 0.0f) r += 360.0f;
+    if (r >= 360.0f) r -= 360.0f;
+    q = x0 + r;
+  }
+  return q;
+}
+
+// Is p inside the cached cell [lo, hi]?  FP64: the definition's half-open
+// cell, closed only at the last node.  FP32: closed on both sides.
+template <typename Real>
+__device__ __forceinline__ bool in_cell(Real p, Real lo, Real hi, bool last) {
+  if constexpr (sizeof(Real) == 8) return p >= lo && (p < hi || (last && p == hi));
+  else return p >= lo && p <= hi;
+}
 
 // Locate p on the longitude axis, using and refreshing the cache.
 // Returns false when the position is out of the domain.
@@ -160,20 +201,15 @@ __device__ __forceinline__ bool locate_lon(const GridArgs &g, Sampler<Real, Stor
   const Real *x = axis<Real>(g, 0);
   if (g.periodic) {
     if (!isfinite(p)) return false;
-    const Real x0 = x[0];
-    Real r = pg_fmod(p - x0, (Real)360);
-    if (r < (Real)0) r += (Real)360;
-    if (r >= (Real)360) r -= (Real)360;
-    q = x0 + r;
+    q = wrap_lon(p, x[0]);
   } else if (!(p >= x[0] && p <= x[g.nx - 1])) {
     return false;
   }
-  const bool last = c.ci == g.nx - 2 && !g.periodic;
-  if (!(c.ci >= 0 && q >= c.xlo && (q < c.xhi || (last && q == c.xhi)))) {
+  if (!(c.ci >= 0 && in_cell<Real>(q, c.xlo, c.xhi, c.ci == g.nx - 2 && !g.periodic))) {
     if (g.periodic && q >= x[g.nx - 1]) {
       c.ci = g.nx - 1; c.ci1 = 0;
       c.xlo = x[g.nx - 1];
-      c.xhi = (Real)g.lon_end;
+      c.xhi = lon_end(g, p);
     } else {
       const int i = axis_search<Real>(g, 0, g.nx, q);
       c.ci = i; c.ci1 = i + 1;
@@ -190,9 +226,8 @@ template <typename Real>
 __device__ __forceinline__ bool locate_axis(const GridArgs &g, int a, int n, int &ci, Real &lo,
                                             Real &hi, Real &rinv, Real p, Real &xi) {
   const Real *x = axis<Real>(g, a);
-  if (!(p >= x[0] && p <= x[n - 1])) return false;
-  const bool last = ci == n - 2;
-  if (!(ci >= 0 && p >= lo && (p < hi || (last && p == hi)))) {
+  if (!(ci >= 0 && in_cell<Real>(p, lo, hi, ci == n - 2))) {
+    if (!(p >= x[0] && p <= x[n - 1])) return false;
     const int i = axis_search<Real>(g, a, n, p);
     ci = i; lo = x[i]; hi = x[i + 1];
     rinv = (Real)1 / (hi - lo);
@@ -202,10 +237,10 @@ __device__ __forceinline__ bool locate_axis(const GridArgs &g, int a, int n, int
   return true;
 }
 
-// Snapshot interval for time t in FP64 (same rules as the definition: the
-// largest s <= nt-2 with T[s] <= t; periodic fields reduce t into
-// [T0, T0 + period) and interpolate from the last snapshot to the first
-// after T[nt-1]).  Writes s0, s1, wrapped tt and the interval bounds.
+// Snapshot interval for time t in FP64 (the definition's rules: the largest
+// s <= nt-2 with T[s] <= t; periodic fields reduce t into [T0, T0 + period)
+// and interpolate from the last snapshot to the first after T[nt-1]).
+// Writes s0, s1, the wrapped time tt and the interval bounds.
 __device__ __forceinline__ bool time_interval(const FieldArgs &f, double t, int &s0, int &s1,
                                               double &tt, double &ta, double &tb) {
   const double *T = f.times;
@@ -236,41 +271,55 @@ __device__ __forceinline__ bool time_interval(const FieldArgs &f, double t, int 
   return true;
 }
 
-// Gather the corner values of the cached cell for snapshots s0 and s1.
+template <typename Real, typename Store, int NF, bool D3>
+__device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
+                                            int sl, int s) {
+  const GridArgs &g = a.g;
+  const Store *base = reinterpret_cast<const Store *>(a.f.tab[s]);
+  if (base == nullptr) {
+    atomicCAS(a.err, 0, (int)DEVERR_SLAB_MISSING);
+    return false;
+  }
+  float sc[3] = {1.f, 1.f, 1.f};
+  if (a.f.scales != nullptr) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) sc[f] = a.f.scales[s * NF + f];
+  }
+#pragma unroll
+  for (int kk = 0; kk < (D3 ? 2 : 1); ++kk) {
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      const size_t row = ((size_t)(c.ck + kk) * g.ny + (size_t)(c.cj + jj)) * g.nx;
+#pragma unroll
+      for (int ii = 0; ii < 2; ++ii) {
+        Real vv[NF];
+        load_node<Real, NF>(base, row + (size_t)(ii ? c.ci1 : c.ci), sc, vv);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) c.v[sl][f][kk * 4 + jj * 2 + ii] = vv[f];
+      }
+    }
+  }
+  return true;
+}
+
+// Make `v` hold the corners of the cached cell for snapshots s0 and s1.  If
+// only the snapshot pair moved on by one, the shared snapshot's corners move
+// from slot 1 to slot 0 and only the new snapshot is read.
 template <typename Real, typename Store, int NF, bool D3>
 __device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
                                        bool steady) {
-  const GridArgs &g = a.g;
-  const int nslab = steady ? 1 : 2;
+  const bool same_cell = c.gi == c.ci && c.gj == c.cj && c.gk == c.ck && c.gi >= 0;
+  if (steady) {
+    if (!gather_slab(a, c, 0, c.s0)) return false;
+  } else if (same_cell && c.s0 == c.gs1) {
 #pragma unroll
-  for (int sl = 0; sl < 2; ++sl) {
-    if (sl >= nslab) break;
-    const int s = sl == 0 ? c.s0 : c.s1;
-    const Store *base = reinterpret_cast<const Store *>(a.f.tab[s]);
-    if (base == nullptr) {
-      atomicCAS(a.err, 0, (int)DEVERR_SLAB_MISSING);
-      return false;
-    }
-    float sc[3] = {1.f, 1.f, 1.f};
-    if (a.f.scales != nullptr) {
+    for (int f = 0; f < NF; ++f)
 #pragma unroll
-      for (int f = 0; f < NF; ++f) sc[f] = a.f.scales[s * NF + f];
-    }
-#pragma unroll
-    for (int kk = 0; kk < (D3 ? 2 : 1); ++kk) {
-#pragma unroll
-      for (int jj = 0; jj < 2; ++jj) {
-#pragma unroll
-        for (int ii = 0; ii < 2; ++ii) {
-          const size_t node = ((size_t)(c.ck + kk) * g.ny + (size_t)(c.cj + jj)) * g.nx +
-                              (size_t)(ii ? c.ci1 : c.ci);
-          Real vv[NF];
-          load_node<Real, NF>(base, node, sc, vv);
-#pragma unroll
-          for (int f = 0; f < NF; ++f) c.v[sl][f][kk * 4 + jj * 2 + ii] = vv[f];
-        }
-      }
-    }
+      for (int q = 0; q < Sampler<Real, Store, NF, D3>::NC; ++q) c.v[0][f][q] = c.v[1][f][q];
+    if (!gather_slab(a, c, 1, c.s1)) return false;
+  } else {
+    if (!gather_slab(a, c, 0, c.s0)) return false;
+    if (!gather_slab(a, c, 1, c.s1)) return false;
   }
   c.gi = c.ci; c.gj = c.cj; c.gk = c.ck; c.gs0 = c.s0; c.gs1 = c.s1;
   return true;
@@ -304,11 +353,9 @@ struct Clock {
   __device__ __forceinline__ double start() const { return t + (double)k * dt; }
 };
 
-// Velocity in position units per second at a stage.  FP64 path: the stage
-// time is t0 + off evaluated in FP64.  FP32 path: off is added to the FP32
-// offset d0 = t0 - ta of the step start inside the cached interval.
-// Returns 0 or a particle status (PG_OOB_*, PG_NAN); -1 for an internal
-// failure already recorded in a.err.
+// Velocity in position units per second at a stage (stage time = step start
+// + off).  Returns 0 or a particle status (PG_OOB_*, PG_NAN); -1 for an
+// internal failure already recorded in a.err.
 template <typename Real, typename Store, int NF, bool D3>
 __device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
                                         Clock &ck, Real off, Real lon, Real lat, Real dep,
@@ -334,7 +381,7 @@ __device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, 
         return -1;
       }
       c.s0 = s0; c.s1 = s1;
-      tau = (Real)((tt - ta) / (tb - ta));
+      tau = (tt - ta) / (tb - ta);
     } else {
       float d = ck.d + (float)off;
       if (!(c.s0 >= 0 && d >= 0.f && d <= c.span)) {
@@ -353,7 +400,7 @@ __device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, 
         d = (float)(tt - ta);
         ck.d = (float)(t0 - c.ta);
       }
-      tau = (Real)fminf(d * c.rspan, 1.0f);
+      tau = fminf(d * c.rspan, 1.0f);
     }
   } else {
     c.s0 = 0; c.s1 = 0;
@@ -374,18 +421,10 @@ __device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, 
   }
   if constexpr (NF == 2) vel[2] = (Real)0;
   if (g.mesh == 1) {
-    vel[0] = vel[0] / ((Real)a.k.deg_m * cos_deg(lat));
-    vel[1] = vel[1] / (Real)a.k.deg_m;
+    vel[0] = lon_rate(vel[0], lat, a.k);
+    vel[1] = lat_rate(vel[1], a.k);
   }
   return 0;
-}
-
-template <typename Real>
-__device__ __forceinline__ Real wrap_lon(Real p, Real x0) {
-  Real r = pg_fmod(p - x0, (Real)360);
-  if (r < (Real)0) r += (Real)360;
-  if (r >= (Real)360) r -= (Real)360;
-  return x0 + r;
 }
 
 template <typename Real>
@@ -403,46 +442,67 @@ __device__ __forceinline__ int out_of_domain(const GridArgs &g, Real lon, Real l
   return 0;
 }
 
+__device__ __forceinline__ double kh_of(const KernArgs &k, double) { return k.kh; }
+__device__ __forceinline__ float kh_of(const KernArgs &k, float) { return k.kh_f; }
+__device__ __forceinline__ double w_of(const KernArgs &k, double) { return k.w_sink; }
+__device__ __forceinline__ float w_of(const KernArgs &k, float) { return k.w_sink_f; }
+
 // One step of Eq. 1.  Returns 0 and updates (lon, lat, dep) on success.
+// RK4 stages run in a loop: stage s samples at (X + k_{s-1} c_s h, t + c_s h)
+// with c = (0, 1/2, 1/2, 1) and accumulates ((k1 + 2 k2) + 2 k3) + k4.
 template <typename Real, typename Store, int NF, bool D3>
 __device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
                                         Clock &ck, Real &lon, Real &lat, Real &dep, Real hr,
                                         uint64_t id, uint32_t stp) {
-  Real k1[3], k2[3], k3[3], k4[3];
-  Real nlon, nlat, ndep;
+  Real kc[3] = {(Real)0, (Real)0, (Real)0};
+  Real acc[3];
+  const Real half = (Real)0.5 * hr;
+  const int nst = a.k.scheme == 0 ? 1 : 4;
   int r;
-  if (a.k.scheme == 0) {
-    if ((r = velocity(a, c, ck, (Real)0, lon, lat, dep, k1))) return r;
-    nlon = lon + k1[0] * hr;
-    nlat = lat + k1[1] * hr;
-    ndep = dep + k1[2] * hr;
+#pragma unroll 1
+  for (int s = 0; s < nst; ++s) {
+    const Real off = s == 0 ? (Real)0 : (s == 3 ? hr : half);
+    Real px = lon, py = lat, pz = dep;
+    if (s > 0) {
+      px = lon + kc[0] * off;
+      py = lat + kc[1] * off;
+      pz = dep + kc[2] * off;
+    }
+    if ((r = velocity(a, c, ck, off, px, py, pz, kc))) return r;
+    if (s == 0) {
+      acc[0] = kc[0]; acc[1] = kc[1]; acc[2] = kc[2];
+    } else if (s == 3) {
+      acc[0] = acc[0] + kc[0]; acc[1] = acc[1] + kc[1]; acc[2] = acc[2] + kc[2];
+    } else {
+      acc[0] = acc[0] + (Real)2 * kc[0];
+      acc[1] = acc[1] + (Real)2 * kc[1];
+      acc[2] = acc[2] + (Real)2 * kc[2];
+    }
+  }
+  Real nlon, nlat, ndep;
+  if (nst == 1) {
+    nlon = lon + acc[0] * hr;
+    nlat = lat + acc[1] * hr;
+    ndep = dep + acc[2] * hr;
   } else {
-    const Real half = (Real)0.5 * hr;
-    if ((r = velocity(a, c, ck, (Real)0, lon, lat, dep, k1))) return r;
-    if ((r = velocity(a, c, ck, half, lon + k1[0] * half, lat + k1[1] * half,
-                      dep + k1[2] * half, k2))) return r;
-    if ((r = velocity(a, c, ck, half, lon + k2[0] * half, lat + k2[1] * half,
-                      dep + k2[2] * half, k3))) return r;
-    if ((r = velocity(a, c, ck, hr, lon + k3[0] * hr, lat + k3[1] * hr, dep + k3[2] * hr,
-                      k4))) return r;
-    nlon = lon + (k1[0] + (Real)2 * k2[0] + (Real)2 * k3[0] + k4[0]) / (Real)6 * hr;
-    nlat = lat + (k1[1] + (Real)2 * k2[1] + (Real)2 * k3[1] + k4[1]) / (Real)6 * hr;
-    ndep = dep + (k1[2] + (Real)2 * k2[2] + (Real)2 * k3[2] + k4[2]) / (Real)6 * hr;
+    nlon = lon + acc[0] / (Real)6 * hr;
+    nlat = lat + acc[1] / (Real)6 * hr;
+    ndep = dep + acc[2] / (Real)6 * hr;
   }
   if (a.k.beh & 1u) {
     Real n1, n2;
     normal_pair(a.k.seed, id, stp, n1, n2);
-    const Real sigma = pg_sqrt((Real)2 * (Real)a.k.kh * pg_fabs(hr));
+    const Real sigma = pg_sqrt((Real)2 * kh_of(a.k, hr) * pg_fabs(hr));
     Real dx = sigma * n1, dy = sigma * n2;
     if (a.g.mesh == 1) {
-      dx = dx / ((Real)a.k.deg_m * cos_deg(nlat));
-      dy = dy / (Real)a.k.deg_m;
+      dx = lon_rate(dx, nlat, a.k);
+      dy = lat_rate(dy, a.k);
     }
     nlon = nlon + dx;
     nlat = nlat + dy;
   }
-  if (a.k.beh & 2u) ndep = ndep + (Real)a.k.w_sink * hr;
-  if (a.g.periodic) nlon = wrap_lon<Real>(nlon, axis<Real>(a.g, 0)[0]);
+  if (a.k.beh & 2u) ndep = ndep + w_of(a.k, hr) * hr;
+  if (a.g.periodic) nlon = wrap_lon(nlon, axis<Real>(a.g, 0)[0]);
   if ((r = out_of_domain<Real>(a.g, nlon, nlat, ndep, D3))) return r;
   lon = nlon; lat = nlat; dep = ndep;
   return 0;
@@ -451,8 +511,11 @@ __device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, 
 // The chunk kernel: each thread advances one particle while its time is
 // before t_stop and t_end (in the direction of dt), shortening only the step
 // that lands on t_end.
+// FP32: at most 128 registers (two 256-thread blocks per SM); measured
+// faster than the unbounded allocation despite a few spilled words, as more
+// resident warps hide the gather and dependency latencies.
 template <typename Real, typename Store, int NF, bool D3>
-__global__ void advect_plain_kernel(StepArgs a) {
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1) advect_plain_kernel(StepArgs a) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long done = 0;
   if (p < a.p.n && a.p.status[p] == 0) {
@@ -468,6 +531,7 @@ __global__ void advect_plain_kernel(StepArgs a) {
     c.reset();
     const double sgn = a.dt > 0.0 ? 1.0 : -1.0;
     Clock ck;
+    ck.dt = a.dt; ck.k = 0; ck.d = 0.f;
     if constexpr (sizeof(Real) == 8) {
       // FP64: the definition's loop, time accumulated step by step.
       while (sgn * (a.t_stop - t) > 0.0 && sgn * (a.t_end - t) > 0.0) {
@@ -491,13 +555,12 @@ __global__ void advect_plain_kernel(StepArgs a) {
       double hlast = a.dt;
       if (n > 0 && sgn * (a.t_end - (t + (double)(n - 1) * a.dt)) < sgn * a.dt)
         hlast = a.t_end - (t + (double)(n - 1) * a.dt);
-      const float hf = (float)a.dt;
-      ck.t = t; ck.dt = a.dt; ck.k = 0;
-      ck.d = 0.f;
+      const float hf = (float)a.dt, hlf = (float)hlast;
+      ck.t = t;
       int k = 0;
       for (; k < n; ++k) {
         ck.k = k;
-        const float h = (k == n - 1) ? (float)hlast : hf;
+        const float h = (k == n - 1) ? hlf : hf;
         const int r = step_one(a, c, ck, lon, lat, dep, (Real)h, id, stp);
         if (r > 0) { st = (uint8_t)r; break; }
         if (r < 0) break;

@@ -229,6 +229,7 @@ GridArgs grid_args(const pg_fieldset *fs) {
     g.inv_df[a] = (float)fs->inv_d[a];
   }
   g.lon_end = fs->lon[0] + 360.0;
+  g.lon_end_f = (float)g.lon_end;
   return g;
 }
 
@@ -924,6 +925,8 @@ pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
   a.f.scales = (fs->storage == PG_F16S || fs->storage == PG_BF16S) ? fs->d_scales : nullptr;
   a.k.scheme = k->scheme; a.k.beh = k->beh; a.k.kh = k->kh; a.k.w_sink = k->w_sink;
   a.k.seed = ps->seed; a.k.deg_m = 1852.0 * 60.0;
+  a.k.deg_m_f = (float)a.k.deg_m; a.k.inv_deg_m_f = (float)(1.0 / a.k.deg_m);
+  a.k.kh_f = (float)k->kh; a.k.w_sink_f = (float)k->w_sink;
   a.dt = dt; a.t_end = t_end;
   a.steps_done = ps->d_counter;
   a.err = ps->d_err;

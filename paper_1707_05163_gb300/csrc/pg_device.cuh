@@ -26,6 +26,7 @@ struct GridArgs {
   double x0[3], inv_d[3];    // first node and 1/spacing (uniform axes)
   float x0f[3], inv_df[3];
   double lon_end;            // lon[0] + 360 (periodic wrap-cell far edge)
+  float lon_end_f;
 };
 
 struct FieldArgs {
@@ -43,6 +44,7 @@ struct KernArgs {
   double kh, w_sink;
   uint64_t seed;
   double deg_m;              // metres per degree
+  float deg_m_f, inv_deg_m_f, kh_f, w_sink_f;   // FP32 copies for the FP32 path
 };
 
 struct PartArgs {
