@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="3d", choices=["3d", "precision"],
+                    help="3d: the FP32 3-D workload (default); precision: 2-D 1/12 deg "
+                         "cell-index + FP16/BF16 form against plain FP32")
+    ap.add_argument("--storage", default="f16", choices=["f16", "bf16"])
     return ap.parse_args()
 
 
@@ -190,6 +194,8 @@ def main():
     import torch
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.workload == "precision":
+        return precision_workload(args, rank, world, local)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -384,6 +390,135 @@ def reference_arm(args, rank, world):
         "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def precision_workload(args, rank, world, local):
+    """2-D surface field on a 1/12 degree grid (4320 x 2160), 60 daily snapshots,
+    50M particles, RK4 dt 1 h for 60 days plus Brownian motion K = 10 m^2/s.
+    Times the cell-index + FP32-offset form on FP16/BF16 storage and plain FP32
+    on FP32 storage on the same workload; reports the speedup, the position
+    error against the FP64 oracle on a 1e5-particle subset, and the diffusion
+    variance against 2Kt."""
+    import torch
+    import ctypes as C
+    import oracle as O
+    import paper_1707_05163_gb300 as pg
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    days = args.days if args.days != 30.0 else 60.0
+    n = args.particles if args.particles != 10_000_000 else 50_000_000
+    nt = 60
+    gf = synth.GlobalField(res_deg=1.0 / 12.0, nz=1, nt=nt, seed=3, period=nt * DAY)
+    kind = 0 if args.storage == "f16" else 1
+    fs_q = pg.FieldSet(gf.lon, gf.lat, None, mesh="spherical", periodic_lon=True, nfields=2,
+                       storage=args.storage)
+    fs_32 = pg.FieldSet(gf.lon, gf.lat, None, mesh="spherical", periodic_lon=True, nfields=2,
+                        storage="f32")
+    for fs in (fs_q, fs_32):
+        fs.set_times(gf.times, gf.period)
+    host32 = np.empty((nt, 2, 1, gf.ny, gf.nx), dtype=np.float32)
+    hostq = np.empty((nt, 2, 1, gf.ny, gf.nx), dtype=np.float32)
+    for s in range(nt):
+        slab = gf.base2d_torch(s, dev).to(torch.float32)[:, None]
+        fs_q.load_snapshot(s, slab)
+        fs_32.load_snapshot(s, slab)
+        host32[s] = slab.cpu().numpy()
+        for f in range(2):
+            q, sc = O.quantise(host32[s, f], kind)
+            assert sc == fs_q.scale(s, f)
+            hostq[s, f] = O.dequantise(q, kind, sc).astype(np.float32)
+        del slab
+    lon, lat, _ = synth.uniform_particles(n, 3, (0.0, 360.0), (-80.0, 80.0), dtype=np.float32)
+    dl, da = torch.from_numpy(lon).to(dev), torch.from_numpy(lat).to(dev)
+    K = 10.0
+    kern = pg.Kernel("rk4", ("brownian",), kh=K)
+    runtime = days * DAY
+
+    def run(fs, pos, timed):
+        ps = pg.ParticleSet(fs, dl, da, pos=pos, seed=3)
+        ps.set_tune(args.block, args.resort_steps, 24)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps = ps.execute(kern, runtime, 3600.0)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        return ps, steps, dt
+
+    rates = {}
+    finals = {}
+    for name, fs, pos in (("cell_" + args.storage, fs_q, "cell"), ("plain_f32", fs_32, "f32")):
+        for _ in range(args.warmup):
+            ps, _, _ = run(fs, pos, False)
+            ps.destroy()
+        tot_s, tot_t = 0, 0.0
+        for _ in range(args.steps):
+            ps, st, dt = run(fs, pos, True)
+            tot_s += st
+            tot_t += dt
+            sub = 100_000
+            g = ps.get()
+            finals[name] = {k: v[:sub] for k, v in g.items()}
+            ps.destroy()
+        rates[name] = tot_s / tot_t
+    # oracle on the first 1e5 ids: on the dequantised field and on the FP32 field
+    sub = min(100_000, n)
+    cores = len(os.sched_getaffinity(0))
+    errs = {}
+    ospec = dict(lon=gf.lon, lat=gf.lat, depth=np.zeros(1), times=gf.times)
+
+    def oracle_final(data):
+        f = O.Field(gf.lon, gf.lat, np.zeros(1), gf.times, data, 1, True, gf.period)
+        st = [np.array(lon[:sub], np.float64), np.array(lat[:sub], np.float64), np.zeros(sub),
+              np.zeros(sub), np.arange(sub, dtype=np.uint64), np.zeros(sub, np.uint32),
+              np.zeros(sub, np.uint8)]
+        t0 = time.perf_counter()
+        done = O.run(f, O.Kernel(O.RK4, O.BROWNIAN, K, 0.0, 3), *st, 3600.0, runtime, runtime,
+                     nthreads=cores)
+        return st, done / (time.perf_counter() - t0)
+
+    def err_cells(g, st):
+        ok = (st[6] == 0) & (g["status"] == 0)
+        dx = 1.0 / 12.0
+        dlon = (g["lon"] - st[0] + 180.0) % 360.0 - 180.0
+        e = np.maximum(np.abs(dlon), np.abs(g["lat"] - st[1])) / dx
+        return {"mean": float(np.mean(e[ok])), "max": float(np.max(e[ok])),
+                "status_equal": bool((st[6] == g["status"]).all())}
+
+    st_q, orate = oracle_final(hostq)
+    st_32, _ = oracle_final(host32)
+    qname = "cell_" + args.storage
+    errs[qname + "_vs_oracle_same_field"] = err_cells(finals[qname], st_q)
+    errs[qname + "_vs_oracle_fp32_field"] = err_cells(finals[qname], st_32)
+    errs["plain_f32_vs_oracle_fp32_field"] = err_cells(finals["plain_f32"], st_32)
+    # diffusion variance against 2 K t on a zero-velocity copy of the grid
+    fz = pg.FieldSet(gf.lon, gf.lat, None, mesh="spherical", periodic_lon=True, nfields=2,
+                     storage=args.storage)
+    fz.set_times(np.zeros(1))
+    fz.load_snapshot(0, np.zeros((2, 1, gf.ny, gf.nx), np.float32))
+    nb = 1_000_000
+    pz = pg.ParticleSet(fz, np.full(nb, 180.0), np.zeros(nb), pos="cell", seed=5)
+    pz.execute(pg.Kernel("rk4", ("brownian",), kh=K), DAY, 3600.0)
+    m = pz.moments()
+    D = 1852.0 * 60.0
+    var_lat = (m[5] / m[0] - (m[2] / m[0]) ** 2) * D * D
+    var_lon = (m[4] / m[0] - (m[1] / m[0]) ** 2) * D * D
+    line = {
+        "metric": METRIC, "value": rates[qname], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 offsets + " + args.storage,
+        "data": "synthetic (seeded k^-3 random streamfunction field, uniform particles)",
+        "config": {"workload": f"2-D RK4 + Brownian K=10, global 1/12 deg 4320x2160, {nt} daily "
+                               f"snapshots ({args.storage} + per-snapshot FP32 scale), {n} "
+                               f"particles, dt 1 h, {days:g} days", "form": "cell index + FP32 offset"},
+        "plain_fp32_rate": rates["plain_f32"], "speedup_vs_plain_fp32": rates[qname] / rates["plain_f32"],
+        "error_cells": errs,
+        "diffusion_variance_over_2Kt_1day": {"lat": var_lat / (2 * K * DAY),
+                                             "lon_at_equator": var_lon / (2 * K * DAY), "n": nb},
+        "cpu_baseline": {"value": orate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {sub} particles, full {days:g}-day horizon"},
+    }
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -26,6 +26,7 @@ UNITS = {
     "field_store.cu": [],
     "sort.cu": [],
     "advect_f64.cu": ["-fmad=false"],
+    "advect_cell.cu": [],
     "advect_f32.cu": ([f"-maxrregcount={os.environ['PG_MAXRREG']}"]
                       if os.environ.get("PG_MAXRREG") else []),
 }

@@ -1,0 +1,378 @@
+// advect_common.cuh -- pieces shared by the advection kernels: node loads
+// of the interleaved field storage, the per-thread cell/snapshot cache
+// (Sampler), the snapshot-interval rules, corner gathers and bi/trilinear
+// interpolation.
+#pragma once
+
+#include "pg_device.cuh"
+
+namespace pg {
+
+// ------------------------------------------------------------ node loads ---
+// Interleaved storage: node (k, j, i) holds its NF field values contiguously
+// (NF = 3 padded to 4), so one vector load fetches U, V[, W] of a corner.
+template <typename Real, int NF>
+__device__ __forceinline__ void load_node(const double *p, size_t node, const float *, Real (&v)[NF]) {
+  if constexpr (NF == 2) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p) + node);
+    v[0] = (Real)a.x; v[1] = (Real)a.y;
+  } else {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p) + 2 * node);
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 2 * node + 1);
+    v[0] = (Real)a.x; v[1] = (Real)a.y; v[2] = (Real)b.x;
+  }
+}
+
+template <typename Real, int NF>
+__device__ __forceinline__ void load_node(const float *p, size_t node, const float *, Real (&v)[NF]) {
+  if constexpr (NF == 2) {
+    const float2 a = __ldg(reinterpret_cast<const float2 *>(p) + node);
+    v[0] = (Real)a.x; v[1] = (Real)a.y;
+  } else {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p) + node);
+    v[0] = (Real)a.x; v[1] = (Real)a.y; v[2] = (Real)a.z;
+  }
+}
+
+// Quantised storage: value = float(code) * scale, rounded in FP32.
+template <typename Real, int NF>
+__device__ __forceinline__ void load_node(const __half *p, size_t node, const float *sc, Real (&v)[NF]) {
+  if constexpr (NF == 2) {
+    const __half2 a = __ldg(reinterpret_cast<const __half2 *>(p) + node);
+    v[0] = (Real)(__low2float(a) * sc[0]); v[1] = (Real)(__high2float(a) * sc[1]);
+  } else {
+    const uint2 a = __ldg(reinterpret_cast<const uint2 *>(p) + node);
+    const __half2 lo = *reinterpret_cast<const __half2 *>(&a.x);
+    const __half2 hi = *reinterpret_cast<const __half2 *>(&a.y);
+    v[0] = (Real)(__low2float(lo) * sc[0]); v[1] = (Real)(__high2float(lo) * sc[1]);
+    v[2] = (Real)(__low2float(hi) * sc[2]);
+  }
+}
+
+template <typename Real, int NF>
+__device__ __forceinline__ void load_node(const __nv_bfloat16 *p, size_t node, const float *sc, Real (&v)[NF]) {
+  if constexpr (NF == 2) {
+    const __nv_bfloat162 a = __ldg(reinterpret_cast<const __nv_bfloat162 *>(p) + node);
+    v[0] = (Real)(__low2float(a) * sc[0]); v[1] = (Real)(__high2float(a) * sc[1]);
+  } else {
+    const uint2 a = __ldg(reinterpret_cast<const uint2 *>(p) + node);
+    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162 *>(&a.x);
+    const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162 *>(&a.y);
+    v[0] = (Real)(__low2float(lo) * sc[0]); v[1] = (Real)(__high2float(lo) * sc[1]);
+    v[2] = (Real)(__low2float(hi) * sc[2]);
+  }
+}
+
+// ------------------------------------------------------- math per Real ---
+__device__ __forceinline__ double pg_floor(double a) { return floor(a); }
+__device__ __forceinline__ float pg_floor(float a) { return floorf(a); }
+__device__ __forceinline__ double pg_sqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float pg_sqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double pg_fabs(double a) { return fabs(a); }
+__device__ __forceinline__ float pg_fabs(float a) { return fabsf(a); }
+// cos(lat in degrees)
+__device__ __forceinline__ double cos_deg(double lat) {
+  const double deg2rad = 3.14159265358979323846 / 180.0;
+  return cos(lat * deg2rad);
+}
+__device__ __forceinline__ float cos_deg(float lat) { return cospif(lat * (1.0f / 180.0f)); }
+
+// u (m/s) -> degrees/s of longitude at latitude lat; v (m/s) -> degrees/s.
+__device__ __forceinline__ double lon_rate(double u, double lat, const KernArgs &k) {
+  return u / (k.deg_m * cos_deg(lat));
+}
+__device__ __forceinline__ float lon_rate(float u, float lat, const KernArgs &k) {
+  return __fdividef(u, k.deg_m_f * cos_deg(lat));
+}
+__device__ __forceinline__ double lat_rate(double v, const KernArgs &k) { return v / k.deg_m; }
+__device__ __forceinline__ float lat_rate(float v, const KernArgs &k) { return v * k.inv_deg_m_f; }
+
+template <typename Real> __device__ __forceinline__ const Real *axis(const GridArgs &g, int a);
+template <> __device__ __forceinline__ const double *axis<double>(const GridArgs &g, int a) {
+  return a == 0 ? g.lon : (a == 1 ? g.lat : g.depth);
+}
+template <> __device__ __forceinline__ const float *axis<float>(const GridArgs &g, int a) {
+  return a == 0 ? g.lonf : (a == 1 ? g.latf : g.depthf);
+}
+template <typename Real> __device__ __forceinline__ Real axis_x0(const GridArgs &g, int a);
+template <> __device__ __forceinline__ double axis_x0<double>(const GridArgs &g, int a) { return g.x0[a]; }
+template <> __device__ __forceinline__ float axis_x0<float>(const GridArgs &g, int a) { return g.x0f[a]; }
+template <typename Real> __device__ __forceinline__ Real axis_inv(const GridArgs &g, int a);
+template <> __device__ __forceinline__ double axis_inv<double>(const GridArgs &g, int a) { return g.inv_d[a]; }
+template <> __device__ __forceinline__ float axis_inv<float>(const GridArgs &g, int a) { return g.inv_df[a]; }
+__device__ __forceinline__ double lon_end(const GridArgs &g, double) { return g.lon_end; }
+__device__ __forceinline__ float lon_end(const GridArgs &g, float) { return g.lon_end_f; }
+
+// Full search on one axis: the largest i <= n-2 with x[i] <= p, given that
+// x[0] <= p <= x[n-1].  Uniform axes start from floor((p - x0) / dx) and
+// correct against the stored nodes; others use bisection.
+template <typename Real>
+__device__ __forceinline__ int axis_search(const GridArgs &g, int a, int n, Real p) {
+  const Real *x = axis<Real>(g, a);
+  int i;
+  if (g.uni[a]) {
+    const Real f = pg_floor((p - axis_x0<Real>(g, a)) * axis_inv<Real>(g, a));
+    i = f < (Real)0 ? 0 : (f > (Real)(n - 2) ? n - 2 : (int)f);
+    while (i > 0 && x[i] > p) --i;
+    while (i < n - 2 && x[i + 1] <= p) ++i;
+  } else {
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+      const int mid = lo + (hi - lo) / 2;
+      if (x[mid] <= p) lo = mid; else hi = mid;
+    }
+    i = lo;
+  }
+  return i;
+}
+
+// ---------------------------------------------------------- the sampler ---
+template <typename Real, typename Store, int NF, bool D3>
+struct Sampler {
+  static constexpr int NC = D3 ? 8 : 4;
+  // cached cell (ci = -1: none) and its bounds
+  int ci, ci1, cj, ck;
+  Real xlo, xhi, ylo, yhi, zlo, zhi;
+  Real rx, ry, rz;            // 1 / (hi - lo), FP32 path only
+  // cached snapshot interval and the snapshots whose corners are held
+  int s0, s1;
+  int gi, gj, gk, gs0, gs1;   // what `v` currently holds (gi = -1: nothing)
+  double ta;                  // FP32 path: interval start in unwrapped time
+  float span, rspan;          // FP32 path
+  Real v[2][NF][NC];
+
+  __device__ __forceinline__ void reset() {
+    ci = -1; cj = -1; ck = -1; s0 = -1; s1 = -1; gi = -1;
+  }
+};
+
+// Reduce a longitude into [x0, x0 + 360).  FP64: the definition's fmod.
+// FP32: stage positions are at most one turn away, so a compare and one
+// add/subtract do (fmod for anything farther).
+__device__ __forceinline__ double wrap_lon(double p, double x0) {
+  double r = fmod(p - x0, 360.0);
+  if (r < 0.0) r += 360.0;
+  if (r >= 360.0) r -= 360.0;
+  return x0 + r;
+}
+__device__ __forceinline__ float wrap_lon(float p, float x0) {
+  float q = p;
+  if (q < x0) q += 360.0f;
+  else if (q >= x0 + 360.0f) q -= 360.0f;
+  if (!(q >= x0 && q < x0 + 360.0f)) {
+    float r = fmodf(p - x0, 360.0f);
+    if (r < 0.0f) r += 360.0f;
+    if (r >= 360.0f) r -= 360.0f;
+    q = x0 + r;
+  }
+  return q;
+}
+
+// Is p inside the cached cell [lo, hi]?  FP64: the definition's half-open
+// cell, closed only at the last node.  FP32: closed on both sides.
+template <typename Real>
+__device__ __forceinline__ bool in_cell(Real p, Real lo, Real hi, bool last) {
+  if constexpr (sizeof(Real) == 8) return p >= lo && (p < hi || (last && p == hi));
+  else return p >= lo && p <= hi;
+}
+
+// Snapshot interval for time t in FP64 (the definition's rules: the largest
+// s <= nt-2 with T[s] <= t; periodic fields reduce t into [T0, T0 + period)
+// and interpolate from the last snapshot to the first after T[nt-1]).
+// Writes s0, s1, the wrapped time tt and the interval bounds.
+__device__ __forceinline__ bool time_interval(const FieldArgs &f, double t, int &s0, int &s1,
+                                              double &tt, double &ta, double &tb) {
+  const double *T = f.times;
+  const int nt = f.nt;
+  tt = t;
+  if (f.period > 0.0) {
+    double r = fmod(t - T[0], f.period);
+    if (r < 0.0) r += f.period;
+    tt = T[0] + r;
+    if (tt >= T[nt - 1]) {
+      s0 = nt - 1; s1 = 0;
+      ta = T[nt - 1]; tb = T[0] + f.period;
+      return true;
+    }
+  }
+  if (!(tt >= T[0] && tt <= T[nt - 1])) return false;
+  int lo = 0, hi = nt - 1;
+  if (s0 >= 0 && s0 <= nt - 2 && T[s0] <= tt && (tt < T[s0 + 1] || (s0 == nt - 2 && tt == T[nt - 1]))) {
+    lo = s0;
+  } else {
+    while (hi - lo > 1) {
+      const int mid = lo + (hi - lo) / 2;
+      if (T[mid] <= tt) lo = mid; else hi = mid;
+    }
+  }
+  s0 = lo; s1 = lo + 1;
+  ta = T[lo]; tb = T[lo + 1];
+  return true;
+}
+
+template <typename Real, typename Store, int NF, bool D3>
+__device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
+                                            int sl, int s) {
+  const GridArgs &g = a.g;
+  const Store *base = reinterpret_cast<const Store *>(a.f.tab[s]);
+  if (base == nullptr) {
+    atomicCAS(a.err, 0, (int)DEVERR_SLAB_MISSING);
+    return false;
+  }
+  float sc[3] = {1.f, 1.f, 1.f};
+  if (a.f.scales != nullptr) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) sc[f] = a.f.scales[s * NF + f];
+  }
+#pragma unroll
+  for (int kk = 0; kk < (D3 ? 2 : 1); ++kk) {
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      const size_t row = ((size_t)(c.ck + kk) * g.ny + (size_t)(c.cj + jj)) * g.nx;
+#pragma unroll
+      for (int ii = 0; ii < 2; ++ii) {
+        Real vv[NF];
+        load_node<Real, NF>(base, row + (size_t)(ii ? c.ci1 : c.ci), sc, vv);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) c.v[sl][f][kk * 4 + jj * 2 + ii] = vv[f];
+      }
+    }
+  }
+  return true;
+}
+
+// Make `v` hold the corners of the cached cell for snapshots s0 and s1.  If
+// only the snapshot pair moved on by one, the shared snapshot's corners move
+// from slot 1 to slot 0 and only the new snapshot is read.
+template <typename Real, typename Store, int NF, bool D3>
+__device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
+                                       bool steady) {
+  const bool same_cell = c.gi == c.ci && c.gj == c.cj && c.gk == c.ck && c.gi >= 0;
+  if (steady) {
+    if (!gather_slab(a, c, 0, c.s0)) return false;
+  } else if (same_cell && c.s0 == c.gs1) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int q = 0; q < Sampler<Real, Store, NF, D3>::NC; ++q) c.v[0][f][q] = c.v[1][f][q];
+    if (!gather_slab(a, c, 1, c.s1)) return false;
+  } else {
+    if (!gather_slab(a, c, 0, c.s0)) return false;
+    if (!gather_slab(a, c, 1, c.s1)) return false;
+  }
+  c.gi = c.ci; c.gj = c.cj; c.gk = c.ck; c.gs0 = c.s0; c.gs1 = c.s1;
+  return true;
+}
+
+// Bilinear weights applied as (w00 f00 + w10 f10) + (w11 f11 + w01 f01);
+// trilinear is linear in zeta between the two levels.
+template <typename Real, int NC>
+__device__ __forceinline__ Real interp_space(const Real (&v)[NC], Real xi, Real eta, Real zeta) {
+  const Real w00 = ((Real)1 - xi) * ((Real)1 - eta);
+  const Real w10 = xi * ((Real)1 - eta);
+  const Real w11 = xi * eta;
+  const Real w01 = ((Real)1 - xi) * eta;
+  const Real a = (w00 * v[0] + w10 * v[1]) + (w11 * v[3] + w01 * v[2]);
+  if constexpr (NC == 4) {
+    return a;
+  } else {
+    const Real b = (w00 * v[4] + w10 * v[5]) + (w11 * v[7] + w01 * v[6]);
+    return ((Real)1 - zeta) * a + zeta * b;
+  }
+}
+
+// Time of the current step.  FP64 path: `t` is the exact step start.  FP32
+// path: the step start is t + k * dt, known to the kernel only as `d`, its
+// FP32 offset inside the cached snapshot interval; the FP64 value is formed
+// only when a stage leaves that interval.
+struct Clock {
+  double t, dt;
+  int k;
+  float d;
+  __device__ __forceinline__ double start() const { return t + (double)k * dt; }
+};
+
+template <typename Real>
+__device__ __forceinline__ int out_of_domain(const GridArgs &g, Real lon, Real lat, Real dep,
+                                             bool d3) {
+  const Real *X = axis<Real>(g, 0);
+  const Real *Y = axis<Real>(g, 1);
+  if (!g.periodic && !(lon >= X[0] && lon <= X[g.nx - 1])) return 1;
+  if (g.periodic && !(lon == lon)) return 1;
+  if (!(lat >= Y[0] && lat <= Y[g.ny - 1])) return 1;
+  if (d3) {
+    const Real *Z = axis<Real>(g, 2);
+    if (!(dep >= Z[0] && dep <= Z[g.nz - 1])) return 2;
+  }
+  return 0;
+}
+
+__device__ __forceinline__ double kh_of(const KernArgs &k, double) { return k.kh; }
+__device__ __forceinline__ float kh_of(const KernArgs &k, float) { return k.kh_f; }
+__device__ __forceinline__ double w_of(const KernArgs &k, double) { return k.w_sink; }
+__device__ __forceinline__ float w_of(const KernArgs &k, float) { return k.w_sink_f; }
+
+// Field values (m/s) at a stage, once the cell (c.ci, c.cj, c.ck) and the
+// fractions (xi, eta, zeta) are known: snapshot interval of the stage time
+// (step start + off), corner gather if the cell or interval changed, spatial
+// interpolation in each snapshot, then linear interpolation in time.
+// Returns 0, PG_NAN (3), or -1 for an internal failure recorded in a.err.
+template <typename Real, typename Store, int NF, bool D3>
+__device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
+                                             Clock &ck, Real off, Real xi, Real eta, Real zeta,
+                                             Real (&vel)[3]) {
+  const bool steady = a.f.nt == 1;
+  Real tau = (Real)0;
+  if (!steady) {
+    if constexpr (sizeof(Real) == 8) {
+      const double ts = ck.t + (double)off;
+      double tt, ta, tb;
+      int s0 = c.s0, s1 = c.s1;
+      if (!time_interval(a.f, ts, s0, s1, tt, ta, tb)) {
+        atomicCAS(a.err, 0, (int)DEVERR_TIME_RANGE);
+        return -1;
+      }
+      c.s0 = s0; c.s1 = s1;
+      tau = (tt - ta) / (tb - ta);
+    } else {
+      float d = ck.d + (float)off;
+      if (!(c.s0 >= 0 && d >= 0.f && d <= c.span)) {
+        const double t0 = ck.start();
+        const double ts = t0 + (double)off;
+        double tt, ta, tb;
+        int s0 = c.s0, s1 = c.s1;
+        if (!time_interval(a.f, ts, s0, s1, tt, ta, tb)) {
+          atomicCAS(a.err, 0, (int)DEVERR_TIME_RANGE);
+          return -1;
+        }
+        c.s0 = s0; c.s1 = s1;
+        c.ta = ts - (tt - ta);              // interval start in unwrapped time
+        c.span = (float)(tb - ta);
+        c.rspan = 1.0f / c.span;
+        d = (float)(tt - ta);
+        ck.d = (float)(t0 - c.ta);
+      }
+      tau = fminf(d * c.rspan, 1.0f);
+    }
+  } else {
+    c.s0 = 0; c.s1 = 0;
+  }
+  if (c.gi != c.ci || c.gj != c.cj || c.gk != c.ck || c.gs0 != c.s0 || c.gs1 != c.s1 ||
+      c.gi < 0) {
+    if (!gather(a, c, steady)) return -1;
+  }
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    Real val = interp_space<Real, Sampler<Real, Store, NF, D3>::NC>(c.v[0][f], xi, eta, zeta);
+    if (!steady) {
+      const Real b = interp_space<Real, Sampler<Real, Store, NF, D3>::NC>(c.v[1][f], xi, eta, zeta);
+      val = val + (b - val) * tau;
+    }
+    if (!(val == val)) return 3;
+    vel[f] = val;
+  }
+  if constexpr (NF == 2) vel[2] = (Real)0;
+  return 0;
+}
+
+}  // namespace pg

@@ -215,6 +215,15 @@ void set_arrays(pg_pset *ps, const PsetArrays &A) {
   ps->time = A.time; ps->id = A.id; ps->step = A.step; ps->status = A.status;
 }
 
+// The device arrays holding a particle set's state, with element sizes.
+std::vector<std::pair<void *, size_t>> state_arrays(const PsetArrays &A, int pos) {
+  if (pos == PG_POS_CELL)
+    return {{A.ci, 4}, {A.cj, 4}, {A.ck, 4}, {A.fx, 4}, {A.fy, 4}, {A.fz, 4},
+            {A.time, 8}, {A.id, 8}, {A.step, 4}, {A.status, 1}};
+  const size_t el = pos_elem(pos);
+  return {{A.x, el}, {A.y, el}, {A.z, el}, {A.time, 8}, {A.id, 8}, {A.step, 4}, {A.status, 1}};
+}
+
 GridArgs grid_args(const pg_fieldset *fs) {
   GridArgs g;
   g.nx = fs->nx; g.ny = fs->ny; g.nz = fs->nz;
@@ -230,8 +239,23 @@ GridArgs grid_args(const pg_fieldset *fs) {
   }
   g.lon_end = fs->lon[0] + 360.0;
   g.lon_end_f = (float)g.lon_end;
+  const double D = 1852.0 * 60.0;
+  for (int a = 0; a < 3; ++a) {
+    g.d[a] = fs->inv_d[a] != 0.0 ? 1.0 / fs->inv_d[a] : 0.0;
+    const std::vector<double> &x = a == 0 ? fs->lon : (a == 1 ? fs->lat : fs->depth);
+    if (x.size() > 1) g.d[a] = (x.back() - x.front()) / (double)(x.size() - 1);
+    g.df[a] = (float)g.d[a];
+    const double metres = (fs->mesh == PG_SPHERICAL && a < 2) ? D * g.d[a] : g.d[a];
+    g.inv_m[a] = metres != 0.0 ? (float)(1.0 / metres) : 0.f;
+  }
   return g;
 }
+
+}  // namespace
+
+GridArgs pg::grid_args_of(const pg_fieldset *fs) { return grid_args(fs); }
+
+namespace {
 
 // ---------------------------------------------------------------- streaming
 
@@ -646,15 +670,32 @@ static pg_status fill_particles(pg_pset *ps, int64_t off, int64_t n, const doubl
                                 double t0, const uint64_t *ids, uint64_t id_base,
                                 cudaStream_t st, double &tmin, double &tmax) {
   const int sm = ps->fs->sm_count;
-  if (ps->pos == PG_POS_CELL) {
-    set_error("cell positions are created by pg_pset_create_cells");
-    return PG_ERR_UNSUPPORTED;
-  }
-  const size_t el = pos_elem(ps->pos);
   pg_status r;
-  if ((r = upload_coord(lon, n, (char *)ps->x + off * el, ps->pos, 0.0, sm, st))) return r;
-  if ((r = upload_coord(lat, n, (char *)ps->y + off * el, ps->pos, 0.0, sm, st))) return r;
-  if ((r = upload_coord(depth, n, (char *)ps->z + off * el, ps->pos, 0.0, sm, st))) return r;
+  if (ps->pos == PG_POS_CELL) {
+    // FP64 positions on the device, then split into cell index + offset
+    double *tmp = nullptr;
+    CU(dev_alloc((void **)&tmp, (size_t)n * 8 * 3));
+    r = upload_coord(lon, n, tmp, PG_POS_F64, 0.0, sm, st);
+    if (!r) r = upload_coord(lat, n, tmp + n, PG_POS_F64, 0.0, sm, st);
+    if (!r) r = upload_coord(depth, n, tmp + 2 * n, PG_POS_F64, ps->fs->depth[0], sm, st);
+    if (!r) {
+      cudaError_t e = launch_to_cell(grid_args(ps->fs), tmp, tmp + n, tmp + 2 * n, ps->ci + off,
+                                     ps->cj + off, ps->ck + off, ps->fx + off, ps->fy + off,
+                                     ps->fz + off, n, sm, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        set_error("cell conversion failed: %s", cudaGetErrorString(e));
+        r = PG_ERR_CUDA;
+      }
+    }
+    dev_free(tmp);
+    if (r) return r;
+  } else {
+    const size_t el = pos_elem(ps->pos);
+    if ((r = upload_coord(lon, n, (char *)ps->x + off * el, ps->pos, 0.0, sm, st))) return r;
+    if ((r = upload_coord(lat, n, (char *)ps->y + off * el, ps->pos, 0.0, sm, st))) return r;
+    if ((r = upload_coord(depth, n, (char *)ps->z + off * el, ps->pos, 0.0, sm, st))) return r;
+  }
   tmin = t0; tmax = t0;
   if (time) {
     CU(cudaMemcpyAsync(ps->time + off, time, n * 8, cudaMemcpyDefault, st));
@@ -697,9 +738,15 @@ pg_status pg_pset_create(pg_fieldset *fs, int64_t n, const double *lon, const do
   ARG(fs && out, "field set and out must not be NULL");
   ARG(n >= 0, "n must be >= 0");
   ARG(n == 0 || (lon && lat), "lon and lat must be given");
-  ARG(pos == PG_POS_F64 || pos == PG_POS_F32, "pos must be PG_POS_F64 or PG_POS_F32 here");
+  ARG(pos == PG_POS_F64 || pos == PG_POS_F32 || pos == PG_POS_CELL,
+      "pos must be PG_POS_F64, PG_POS_F32 or PG_POS_CELL");
   ARG(std::isfinite(t0), "t0 must be finite");
-  ARG(!(pos == PG_POS_F32 && fs->storage == PG_F64), "FP32 positions need FP32/FP16/BF16 storage");
+  ARG(!(pos != PG_POS_F64 && fs->storage == PG_F64),
+      "FP32 or cell positions need FP32/FP16/BF16 storage");
+  if (pos == PG_POS_CELL && !(fs->uni[0] && fs->uni[1] && (fs->nz == 1 || fs->uni[2]))) {
+    set_error("cell positions need uniformly spaced axes");
+    return PG_ERR_UNSUPPORTED;
+  }
   auto *ps = new pg_pset();
   ps->fs = fs; ps->pos = pos; ps->seed = seed;
   PsetArrays A;
@@ -751,7 +798,12 @@ pg_status pg_pset_add(pg_pset *ps, int64_t n, const double *lon, const double *l
     auto cp = [&](void *d, const void *s, size_t b) {
       if (e == cudaSuccess && b) e = cudaMemcpy(d, s, b, cudaMemcpyDeviceToDevice);
     };
-    cp(B.x, A.x, m * el); cp(B.y, A.y, m * el); cp(B.z, A.z, m * el);
+    if (ps->pos == PG_POS_CELL) {
+      cp(B.ci, A.ci, m * 4); cp(B.cj, A.cj, m * 4); cp(B.ck, A.ck, m * 4);
+      cp(B.fx, A.fx, m * 4); cp(B.fy, A.fy, m * 4); cp(B.fz, A.fz, m * 4);
+    } else {
+      cp(B.x, A.x, m * el); cp(B.y, A.y, m * el); cp(B.z, A.z, m * el);
+    }
     cp(B.time, A.time, m * 8); cp(B.id, A.id, m * 8); cp(B.step, A.step, m * 4);
     cp(B.status, A.status, m);
     if (e != cudaSuccess) {
@@ -794,6 +846,21 @@ pg_status pg_pset_get(const pg_pset *ps, double *lon, double *lat, double *depth
   const int64_t n = ps->n;
   if (n == 0) return PG_OK;
   double *tmp = nullptr;
+  if (ps->pos == PG_POS_CELL && (lon || lat || depth)) {
+    CU(dev_alloc((void **)&tmp, n * 8 * 3));
+    cudaError_t e = launch_from_cell(grid_args(ps->fs), ps->ci, ps->cj, ps->ck, ps->fx, ps->fy,
+                                     ps->fz, tmp, tmp + n, tmp + 2 * n, n, ps->fs->sm_count, st);
+    if (e == cudaSuccess && lon) e = cudaMemcpyAsync(lon, tmp, n * 8, cudaMemcpyDefault, st);
+    if (e == cudaSuccess && lat) e = cudaMemcpyAsync(lat, tmp + n, n * 8, cudaMemcpyDefault, st);
+    if (e == cudaSuccess && depth) e = cudaMemcpyAsync(depth, tmp + 2 * n, n * 8, cudaMemcpyDefault, st);
+    if (e != cudaSuccess) {
+      cudaStreamSynchronize(st);
+      dev_free(tmp);
+      set_error("copy failed: %s", cudaGetErrorString(e));
+      return PG_ERR_CUDA;
+    }
+    lon = lat = depth = nullptr;
+  }
   if (ps->pos == PG_POS_F32 && (lon || lat || depth)) CU(dev_alloc((void **)&tmp, n * 8));
   auto coord = [&](void *src, double *dst) -> pg_status {
     if (!dst) return PG_OK;
@@ -993,7 +1060,10 @@ pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
       }
       CU(cudaEventRecord(ps->ev[ps->ev_used], st));
     }
-    CU(launch_advect_plain(a, ps->pos, fs->storage, ps->tune.block, st));
+    a.p.ci = ps->ci; a.p.cj = ps->cj; a.p.ck = ps->ck;
+    a.p.fx = ps->fx; a.p.fy = ps->fy; a.p.fz = ps->fz;
+    if (ps->pos == PG_POS_CELL) CU(launch_advect_cell(a, fs->storage, ps->tune.block, st));
+    else CU(launch_advect_plain(a, ps->pos, fs->storage, ps->tune.block, st));
     if (ps->timing) {
       CU(cudaEventRecord(ps->ev[ps->ev_used + 1], st));
       ps->ev_used += 2;
@@ -1060,38 +1130,25 @@ pg_status pg_pset_save(const pg_pset *ps, const char *path) {
   clear_error();
   ARG(ps && path, "arguments must not be NULL");
   const int64_t n = ps->n;
-  std::vector<double> lon(n), lat(n), dep(n), tim(n);
-  std::vector<uint64_t> ids(n);
-  std::vector<uint32_t> stp(n);
-  std::vector<uint8_t> sta(n);
-  // raw position bytes keep FP32 state bit for bit
-  const size_t el = pos_elem(ps->pos);
-  std::vector<char> x(n * el), y(n * el), z(n * el);
-  if (n) {
-    CU(cudaMemcpy(x.data(), ps->x, n * el, cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(y.data(), ps->y, n * el, cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(z.data(), ps->z, n * el, cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(tim.data(), ps->time, n * 8, cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(ids.data(), ps->id, n * 8, cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(stp.data(), ps->step, n * 4, cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(sta.data(), ps->status, n, cudaMemcpyDeviceToHost));
+  // raw array bytes keep FP32 and cell-form state bit for bit
+  const auto arrays = state_arrays(arrays_of(ps), ps->pos);
+  std::vector<std::vector<char>> host(arrays.size());
+  for (size_t q = 0; q < arrays.size(); ++q) {
+    host[q].resize((size_t)n * arrays[q].second);
+    if (n) CU(cudaMemcpy(host[q].data(), arrays[q].first, host[q].size(), cudaMemcpyDeviceToHost));
   }
   FILE *f = fopen(path, "wb");
   if (!f) {
     set_error("cannot open %s for writing", path);
     return PG_ERR_ARG;
   }
-  const char magic[8] = {'P', 'G', 'P', 'S', 'E', 'T', '0', '1'};
+  const char magic[8] = {'P', 'G', 'P', 'S', 'E', 'T', '0', '2'};
   const int32_t pos = ps->pos;
   bool ok = fwrite(magic, 8, 1, f) == 1 && fwrite(&pos, 4, 1, f) == 1 &&
             fwrite(&n, 8, 1, f) == 1 && fwrite(&ps->seed, 8, 1, f) == 1 &&
             fwrite(&ps->t_min, 8, 1, f) == 1 && fwrite(&ps->t_max, 8, 1, f) == 1;
-  if (ok && n) {
-    ok = fwrite(x.data(), el, n, f) == (size_t)n && fwrite(y.data(), el, n, f) == (size_t)n &&
-         fwrite(z.data(), el, n, f) == (size_t)n && fwrite(tim.data(), 8, n, f) == (size_t)n &&
-         fwrite(ids.data(), 8, n, f) == (size_t)n && fwrite(stp.data(), 4, n, f) == (size_t)n &&
-         fwrite(sta.data(), 1, n, f) == (size_t)n;
-  }
+  for (size_t q = 0; ok && q < host.size(); ++q)
+    if (n) ok = fwrite(host[q].data(), 1, host[q].size(), f) == host[q].size();
   if (fclose(f) != 0) ok = false;
   if (!ok) {
     set_error("write to %s failed", path);
@@ -1113,24 +1170,19 @@ pg_status pg_pset_restore(pg_fieldset *fs, const char *path, pg_pset **out) {
   int64_t n = 0;
   uint64_t seed = 0;
   double tmin = 0, tmax = 0;
-  bool ok = fread(magic, 8, 1, f) == 1 && memcmp(magic, "PGPSET01", 8) == 0 &&
+  bool ok = fread(magic, 8, 1, f) == 1 && memcmp(magic, "PGPSET02", 8) == 0 &&
             fread(&pos, 4, 1, f) == 1 && fread(&n, 8, 1, f) == 1 && fread(&seed, 8, 1, f) == 1 &&
             fread(&tmin, 8, 1, f) == 1 && fread(&tmax, 8, 1, f) == 1 &&
-            (pos == PG_POS_F64 || pos == PG_POS_F32) && n >= 0;
-  const size_t el = ok ? pos_elem(pos) : 0;
-  std::vector<char> x, y, z;
-  std::vector<double> tim;
-  std::vector<uint64_t> ids;
-  std::vector<uint32_t> stp;
-  std::vector<uint8_t> sta;
+            (pos == PG_POS_F64 || pos == PG_POS_F32 || pos == PG_POS_CELL) && n >= 0 &&
+            n < ((int64_t)1 << 40);
+  std::vector<std::vector<char>> host;
   if (ok) {
-    x.resize(n * el); y.resize(n * el); z.resize(n * el);
-    tim.resize(n); ids.resize(n); stp.resize(n); sta.resize(n);
-    if (n)
-      ok = fread(x.data(), el, n, f) == (size_t)n && fread(y.data(), el, n, f) == (size_t)n &&
-           fread(z.data(), el, n, f) == (size_t)n && fread(tim.data(), 8, n, f) == (size_t)n &&
-           fread(ids.data(), 8, n, f) == (size_t)n && fread(stp.data(), 4, n, f) == (size_t)n &&
-           fread(sta.data(), 1, n, f) == (size_t)n;
+    const auto sizes = state_arrays(PsetArrays(), pos);
+    host.resize(sizes.size());
+    for (size_t q = 0; ok && q < sizes.size(); ++q) {
+      host[q].resize((size_t)n * sizes[q].second);
+      if (n) ok = fread(host[q].data(), 1, host[q].size(), f) == host[q].size();
+    }
   }
   fclose(f);
   if (!ok) {
@@ -1146,13 +1198,10 @@ pg_status pg_pset_restore(pg_fieldset *fs, const char *path, pg_pset **out) {
     PsetArrays B;
     r = alloc_arrays(B, pos, n);
     if (r) { pg_pset_destroy(ps); return r; }
+    const auto arrays = state_arrays(B, pos);
     cudaError_t e = cudaSuccess;
-    auto cp = [&](void *d, const void *s, size_t b) {
-      if (e == cudaSuccess) e = cudaMemcpy(d, s, b, cudaMemcpyHostToDevice);
-    };
-    cp(B.x, x.data(), n * el); cp(B.y, y.data(), n * el); cp(B.z, z.data(), n * el);
-    cp(B.time, tim.data(), n * 8); cp(B.id, ids.data(), n * 8); cp(B.step, stp.data(), n * 4);
-    cp(B.status, sta.data(), n);
+    for (size_t q = 0; e == cudaSuccess && q < arrays.size(); ++q)
+      e = cudaMemcpy(arrays[q].first, host[q].data(), host[q].size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       B.free_all();
       pg_pset_destroy(ps);

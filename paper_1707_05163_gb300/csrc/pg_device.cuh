@@ -27,6 +27,11 @@ struct GridArgs {
   float x0f[3], inv_df[3];
   double lon_end;            // lon[0] + 360 (periodic wrap-cell far edge)
   float lon_end_f;
+  // uniform axes, cell form: spacing, and metres -> cells factors (lon on a
+  // sphere: 1 / (D dlon), still to be divided by cos(lat))
+  double d[3];
+  float df[3];
+  float inv_m[3];
 };
 
 struct FieldArgs {

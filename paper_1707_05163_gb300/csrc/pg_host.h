@@ -135,6 +135,19 @@ cudaError_t launch_repack(const void *src, int src_dtype, int nf, size_t nodes, 
 cudaError_t launch_advect_plain(const StepArgs &a, int real, int storage, int block,
                                 cudaStream_t st);
 
+// Advection chunk for cell-index + offset positions.
+cudaError_t launch_advect_cell(const StepArgs &a, int storage, int block, cudaStream_t st);
+cudaError_t launch_to_cell(const GridArgs &g, const double *lon, const double *lat,
+                           const double *dep, int32_t *ci, int32_t *cj, int32_t *ck, float *fx,
+                           float *fy, float *fz, int64_t n, int sm, cudaStream_t st);
+cudaError_t launch_from_cell(const GridArgs &g, const int32_t *ci, const int32_t *cj,
+                             const int32_t *ck, const float *fx, const float *fy, const float *fz,
+                             double *lon, double *lat, double *dep, int64_t n, int sm,
+                             cudaStream_t st);
+
+// Grid argument block of a field set (defined in capi.cu).
+GridArgs grid_args_of(const pg_fieldset *fs);
+
 // Element size of one position coordinate for a position form.
 inline size_t pos_elem(int pos) { return pos == PG_POS_F64 ? 8 : 4; }
 inline size_t storage_elem(int storage) {

@@ -295,10 +295,10 @@ __device__ __forceinline__ void pos_of(const Real *x, const Real *y, const Real 
                                        const float *fx, const float *fy, const float *fz,
                                        const GridArgs &g, int64_t p, double &a, double &b,
                                        double &c) {
-  if (ci) {
-    a = g.lon[ci[p]] + (double)fx[p] * (g.lon[ci[p] + 1] - g.lon[ci[p]]);
-    b = g.lat[cj[p]] + (double)fy[p] * (g.lat[cj[p] + 1] - g.lat[cj[p]]);
-    c = ck ? g.depth[ck[p]] + (double)fz[p] * (g.depth[ck[p] + 1] - g.depth[ck[p]]) : 0.0;
+  if (ci) {   // uniform axes: x0 + (index + offset) * spacing
+    a = g.x0[0] + ((double)ci[p] + (double)fx[p]) * g.d[0];
+    b = g.x0[1] + ((double)cj[p] + (double)fy[p]) * g.d[1];
+    c = ck ? g.x0[2] + ((double)ck[p] + (double)fz[p]) * g.d[2] : 0.0;
   } else {
     a = (double)x[p]; b = (double)y[p]; c = (double)z[p];
   }
@@ -354,8 +354,7 @@ cudaError_t launch_moments(const pg_pset *ps_c, double *out7, cudaStream_t st) {
       return e;
   }
   const pg_fieldset *fs = ps->fs;
-  GridArgs g;
-  g.lon = fs->d_axes64; g.lat = fs->d_axes64 + fs->nx; g.depth = fs->d_axes64 + fs->nx + fs->ny;
+  const GridArgs g = grid_args_of(fs);
   double *partial = ps->diag_scratch;
   double *res = partial + kMomBlocks * 7;
   const int64_t n = ps->n;

@@ -317,3 +317,37 @@ class GlobalField:
             data = np.stack([self.slab(s) for s in range(len(self.times))])
         return FieldSpec(self.lon, self.lat, self.depth, self.times, data, SPHERICAL, True,
                          self.period, self.nfields, None if materialise else self.slab)
+
+
+def _global_base2d_torch(self, s, device):
+    """:meth:`GlobalField.base2d` evaluated with torch on `device` (FP64).
+
+    Same formulas as the numpy version (values agree to rounding); used to
+    build large fields quickly.  Whatever consumes a field built this way (the
+    CUDA path and the oracle) must read the same arrays."""
+    import torch
+    t = float(self.times[s])
+    amp = torch.as_tensor(self._amp, device=device)
+
+    def psi(phase, freq):
+        ph = torch.as_tensor(phase, device=device) + 2 * np.pi * torch.as_tensor(
+            freq, device=device) * (t / self.period)
+        spec = torch.polar(amp, ph)
+        return torch.fft.irfft2(spec, s=(self.ny, self.nx)) * (self.nx * self.ny)
+
+    taper = torch.as_tensor(self._taper, device=device)
+    coslat = torch.as_tensor(self._coslat, device=device)
+    p = psi(self._phase, self._freq) * taper
+    dlam = np.deg2rad(360.0 / self.nx)
+    dphi = np.deg2rad(180.0 / self.ny)
+    dpsi_dlam = (torch.roll(p, -1, dims=1) - torch.roll(p, 1, dims=1)) / (2 * dlam)
+    dpsi_dphi = torch.gradient(p, spacing=dphi, dim=0)[0]
+    u = -dpsi_dphi / EARTH_R
+    v = dpsi_dlam / (EARTH_R * coslat)
+    out = [u * self._scale_uv, v * self._scale_uv]
+    if self.with_w:
+        out.append(psi(self._phase_w, self._freq_w) * taper * self._scale_w)
+    return torch.stack(out)
+
+
+GlobalField.base2d_torch = _global_base2d_torch
