@@ -366,7 +366,12 @@ __device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, St
     Real val = interp_space<Real, Sampler<Real, Store, NF, D3>::NC>(c.v[0][f], xi, eta, zeta);
     if (!steady) {
       const Real b = interp_space<Real, Sampler<Real, Store, NF, D3>::NC>(c.v[1][f], xi, eta, zeta);
-      val = val + (b - val) * tau;
+      // FP64: the definition's a + (b - a) tau.  FP32: (1 - tau) a + tau b,
+      // exact at both ends, so a stage time on a snapshot gives the same
+      // value from either neighbouring interval (results do not depend on
+      // which interval a thread happens to have cached).
+      if constexpr (sizeof(Real) == 8) val = val + (b - val) * tau;
+      else val = fmaf(tau, b, (1.0f - tau) * val);
     }
     if (!(val == val)) return 3;
     vel[f] = val;
