@@ -239,6 +239,32 @@ PG_API pg_status pg_pset_resort(pg_pset *ps, void *stream);
  * sum depth^2, accumulated in FP64 in a fixed order (deterministic). */
 PG_API pg_status pg_pset_moments(const pg_pset *ps, double out[7], void *stream);
 
+/* FP64 moments of caller-owned particle arrays without allocating memory.
+ * The paper has no counterpart: this call exists for callers that must not
+ * allocate device memory while they run -- processes whose device memory
+ * all belongs to their own allocator from start-up, and latency-critical
+ * loops that cannot afford cudaMalloc/cudaFree round trips (cudaFree also
+ * synchronises the whole device).  It sums as pg_pset_moments does (count,
+ * sums and sums of squares of lon, lat, depth over particles whose status is
+ * 0), over device arrays lon[n], lat[n], depth[n] (NULL: zeros) and
+ * status[n] (NULL: all alive), and writes the 7 doubles to the device
+ * pointer `out`, asynchronously on `stream`.
+ *   - No allocation: the partial sums live in a fixed device array of the
+ *     library (229,376 bytes, held on every GPU that loads the library until
+ *     the process exits).  n may be at most 268,435,456; larger n returns
+ *     PG_ERR_ARG before any work.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the array and leaves the last call's partial sums in
+ *     it (each call overwrites all it reads, so nothing needs clearing).
+ *     Calls whose work overlaps on the GPU, on any streams, race on it:
+ *     order them on one stream or synchronise between them.
+ *   - Errors: PG_ERR_ARG (NULL pointers, n out of range), PG_ERR_CUDA. */
+PG_API pg_status pg_moments_f64_noalloc(const double *lon, const double *lat,
+                                        const double *depth, const uint8_t *status, int64_t n,
+                                        double *out, void *stream);
+
 /* Checkpoint: write / read the complete particle state (positions, times,
  * ids, step counters, status, seed) to a file.  Restoring gives a set that
  * continues bit-identically. */

@@ -79,6 +79,7 @@ _SIGS = {
     "pg_pset_kernel_timing": ([_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
     "pg_launch_count": ([C.POINTER(C.c_int64)], C.c_int),
     "pg_fieldset_stats": ([_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
+    "pg_moments_f64_noalloc": ([_P, _P, _P, _P, C.c_int64, _P, _P], C.c_int),
 }
 
 _lock = threading.Lock()

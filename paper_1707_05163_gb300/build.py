@@ -27,6 +27,7 @@ UNITS = {
     "sort.cu": [],
     "advect_f64.cu": ["-fmad=false"],
     "advect_cell.cu": [],
+    "moments_noalloc.cu": [],
     "advect_f32.cu": ([f"-maxrregcount={os.environ['PG_MAXRREG']}"]
                       if os.environ.get("PG_MAXRREG") else []),
 }
