@@ -81,7 +81,7 @@ def measured_peaks():
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("advect_plain.cuh", "advect_f32.cu", "pg_device.cuh"):
+    for f in ("advect_common.cuh", "advect_plain.cuh", "advect_f32.cu", "pg_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1707_05163_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
