@@ -230,6 +230,27 @@ PG_API pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, dou
                      double output_dt, pg_output_cb out, void *user, void *stream,
                      int64_t *steps_done);
 
+/* Batched form: advance many releases (the repeated releases of Sect. 3),
+ * each a particle set with its own kernel, dt (> 0) and runtime, over one
+ * field set with all snapshots resident.  Every `window` seconds of
+ * simulated time is one launch of a persistent kernel that walks a work list
+ * of (release, tile) pairs, heaviest first.  Releases of at least 65,536
+ * particles are Morton re-sorted every tune->resort_steps windows (0: never;
+ * in this call the field counts windows, not steps).  tune == NULL runs the
+ * autotuner: it times each block size in {64, 128, 256} with each re-sort
+ * interval in {never, 1, 2} over the first (up to) four windows from a saved
+ * copy of the state, restores the state and keeps the fastest; with
+ * `tune_cache` (a file path, may be NULL) the choice is stored under a key of
+ * the GPU name and the workload's shape and reused by later calls.  The
+ * choice is written to *chosen if non-NULL.  use_graph != 0 captures the whole
+ * window loop in one CUDA graph and launches it once.  Positions must be
+ * PG_POS_F32.  Each release runs from its particle set's start time for its
+ * runtime; particle-steps taken go to *steps_done. */
+PG_API pg_status pg_execute_batch(int nrel, pg_pset *const *psets, const pg_kernel *const *kernels,
+                                  const double *runtime, const double *dt, double window,
+                                  const pg_tune *tune, pg_tune *chosen, const char *tune_cache,
+                                  int use_graph, void *stream, int64_t *steps_done);
+
 /* Morton re-sort now: order particles by the Morton code of their cell
  * indices and move deleted particles behind the alive ones. */
 PG_API pg_status pg_pset_resort(pg_pset *ps, void *stream);

@@ -80,6 +80,8 @@ _SIGS = {
     "pg_launch_count": ([C.POINTER(C.c_int64)], C.c_int),
     "pg_fieldset_stats": ([_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
     "pg_moments_f64_noalloc": ([_P, _P, _P, _P, C.c_int64, _P, _P], C.c_int),
+    "pg_execute_batch": ([C.c_int, _P, _P, _P, _P, C.c_double, C.POINTER(Tune), C.POINTER(Tune),
+                          C.c_char_p, C.c_int, _P, C.POINTER(C.c_int64)], C.c_int),
 }
 
 _lock = threading.Lock()

@@ -318,3 +318,26 @@ class ParticleSet:
             self.destroy()
         except Exception:
             pass
+
+
+def execute_batch(psets, kernels, runtimes, dts, window=86400.0, tune=None, tune_cache=None,
+                  use_graph=True, stream=None):
+    """Advance many releases in one persistent launch per window (pg_execute_batch).
+
+    ``tune`` = (block, resort_windows) or None for the autotuner.  Returns
+    (particle-steps, (block, resort_windows) used)."""
+    lib = N.load()
+    nrel = len(psets)
+    ps_arr = (C.c_void_p * nrel)(*[p.h.value for p in psets])
+    k_arr = (C.c_void_p * nrel)(*[k.h.value for k in kernels])
+    rt = np.ascontiguousarray(runtimes, dtype=np.float64)
+    dt = np.ascontiguousarray(dts, dtype=np.float64)
+    t_in = N.Tune(int(tune[0]), int(tune[1]), 0) if tune is not None else None
+    chosen = N.Tune()
+    steps = C.c_int64()
+    N.check(lib.pg_execute_batch(nrel, ps_arr, k_arr, rt.ctypes.data, dt.ctypes.data,
+                                 float(window), C.byref(t_in) if t_in is not None else None,
+                                 C.byref(chosen),
+                                 str(tune_cache).encode() if tune_cache else None,
+                                 int(bool(use_graph)), _stream(stream), C.byref(steps)))
+    return steps.value, (chosen.block, chosen.resort_steps)

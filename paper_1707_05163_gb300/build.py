@@ -28,6 +28,7 @@ UNITS = {
     "advect_f64.cu": ["-fmad=false"],
     "advect_cell.cu": [],
     "moments_noalloc.cu": [],
+    "batch.cu": [],
     "advect_f32.cu": ([f"-maxrregcount={os.environ['PG_MAXRREG']}"]
                       if os.environ.get("PG_MAXRREG") else []),
 }

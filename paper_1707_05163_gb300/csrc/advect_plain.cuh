@@ -157,15 +157,11 @@ __device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, 
 
 // The chunk kernel: each thread advances one particle while its time is
 // before t_stop and t_end (in the direction of dt), shortening only the step
-// that lands on t_end.
-// FP32: at most 128 registers (two 256-thread blocks per SM); measured
-// faster than the unbounded allocation despite a few spilled words, as more
-// resident warps hide the gather and dependency latencies.
+// that lands on t_end.  Returns the number of steps taken.
 template <typename Real, typename Store, int NF, bool D3>
-__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1) advect_plain_kernel(StepArgs a) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ unsigned long long advance_particle(const StepArgs &a, int64_t p) {
   unsigned long long done = 0;
-  if (p < a.p.n && a.p.status[p] == 0) {
+  {
     Real *X = reinterpret_cast<Real *>(a.p.x);
     Real *Y = reinterpret_cast<Real *>(a.p.y);
     Real *Z = reinterpret_cast<Real *>(a.p.z);
@@ -223,10 +219,78 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1) advect_plain_k
     a.p.step[p] = stp;
     a.p.status[p] = st;
   }
-  // one atomic per warp for the particle-step counter
+  return done;
+}
+
+// One atomic per warp for the particle-step counter.
+__device__ __forceinline__ void count_steps(unsigned long long done, unsigned long long *counter) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);
-  if ((threadIdx.x & 31) == 0 && done) atomicAdd(a.steps_done, done);
+  if ((threadIdx.x & 31) == 0 && done) atomicAdd(counter, done);
+}
+
+// FP32: at most 128 registers (two 256-thread blocks per SM); measured
+// faster than the unbounded allocation despite a few spilled words, as more
+// resident warps hide the gather and dependency latencies.
+template <typename Real, typename Store, int NF, bool D3>
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1) advect_plain_kernel(StepArgs a) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long done = 0;
+  if (p < a.p.n && a.p.status[p] == 0) done = advance_particle<Real, Store, NF, D3>(a, p);
+  count_steps(done, a.steps_done);
+}
+
+// Batched form: a persistent kernel walks a device work list of tiles
+// (release, first particle); each CTA takes the next tile with one atomic,
+// so releases of very different cost (dt from 10 min to 2 h) balance across
+// the SMs.  Each release brings its own particle arrays, kernel, dt and end
+// time (table `rel`); the field is shared.
+struct BatchRelease {
+  PartArgs p;
+  KernArgs k;
+  double dt, t_end;
+};
+
+struct BatchArgs {
+  GridArgs g;
+  FieldArgs f;
+  const BatchRelease *rel;
+  const int2 *tiles;      // (release, first particle), heaviest first
+  int ntiles;
+  int *next_tile;         // work-list cursor, zeroed before every launch
+  double t_stop;
+  unsigned long long *steps_done;
+  int *err;
+};
+
+template <typename Store, int NF, bool D3>
+__global__ void __launch_bounds__(256, 2) advect_batch_kernel(BatchArgs b) {
+  __shared__ int tile;
+  unsigned long long done = 0;
+  for (;;) {
+    if (threadIdx.x == 0) tile = atomicAdd(b.next_tile, 1);
+    __syncthreads();
+    const int t = tile;
+    __syncthreads();
+    if (t >= b.ntiles) break;
+    const int2 td = b.tiles[t];
+    const BatchRelease *R = b.rel + td.x;
+    const int64_t p = (int64_t)td.y + threadIdx.x;
+    if (p < R->p.n && R->p.status[p] == 0) {
+      StepArgs a;
+      a.g = b.g;
+      a.f = b.f;
+      a.k = R->k;
+      a.p = R->p;
+      a.dt = R->dt;
+      a.t_stop = b.t_stop;
+      a.t_end = R->t_end;
+      a.steps_done = b.steps_done;
+      a.err = b.err;
+      done += advance_particle<float, Store, NF, D3>(a, p);
+    }
+  }
+  count_steps(done, b.steps_done);
 }
 
 }  // namespace pg

@@ -29,19 +29,25 @@ struct MortonSpec {
   int total;
 };
 
-MortonSpec morton_spec(const pg_fieldset *fs) {
+// Bits of the Morton key: all cell bits of each axis, then the finest bits
+// dropped (largest axis first) until the key has at most about twice as many
+// buckets as particles (between 2^8 and 2^22 buckets).
+MortonSpec morton_spec(const pg_fieldset *fs, int64_t n) {
+  int max_bits = 1;
+  while (max_bits < kMaxKeyBits && ((int64_t)1 << max_bits) < 2 * n) ++max_bits;
+  if (max_bits < 8) max_bits = 8;
   MortonSpec m{};
-  const int n[3] = {fs->nx, fs->ny, fs->nz};
+  const int nodes[3] = {fs->nx, fs->ny, fs->nz};
   m.dims = fs->nz > 1 ? 3 : 2;
   m.total = 0;
   for (int d = 0; d < m.dims; ++d) {
     int b = 0;
-    while ((1 << b) < n[d]) ++b;
+    while ((1 << b) < nodes[d]) ++b;
     m.bits[d] = b;
     m.shift[d] = 0;
     m.total += b;
   }
-  while (m.total > kMaxKeyBits) {
+  while (m.total > max_bits) {
     int w = 0;
     for (int d = 1; d < m.dims; ++d)
       if (m.bits[d] > m.bits[w]) w = d;
@@ -189,15 +195,16 @@ cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t m, uint32_
 
 }  // namespace
 
-cudaError_t launch_resort(pg_pset *ps, cudaStream_t st, int64_t *n_alive) {
+// n_alive == nullptr: keep the particle arrays where they are (the sorted
+// copy is copied back) and read nothing back to the host, so the whole
+// re-sort is a fixed sequence of device operations (capturable in a graph).
+// Scratch and the second array set must then already exist
+// (prepare_resort).
+cudaError_t prepare_resort(pg_pset *ps) {
   const int64_t n = ps->n;
-  *n_alive = n;
   if (n == 0) return cudaSuccess;
-  if (n >= (int64_t)0xFFFFFFFFll) return cudaErrorInvalidValue;
-  const pg_fieldset *fs = ps->fs;
-  const MortonSpec m = morton_spec(fs);
-  const uint32_t dead = 1u << m.total;
-  const int64_t nb = (int64_t)dead + 1;
+  const MortonSpec m = morton_spec(ps->fs, n);
+  const int64_t nb = ((int64_t)1 << m.total) + 1;
   const int64_t tiles = (nb + kScanTile - 1) / kScanTile;
   const size_t need = sizeof(uint32_t) * ((size_t)n * 2 + (size_t)nb * 2 + (size_t)tiles * 2 + 1);
   cudaError_t e;
@@ -214,6 +221,20 @@ cudaError_t launch_resort(pg_pset *ps, cudaStream_t st, int64_t *n_alive) {
     if (alloc_arrays(ps->alt, ps->pos, ps->cap) != PG_OK) return cudaErrorMemoryAllocation;
     ps->alt_cap = ps->cap;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_resort(pg_pset *ps, cudaStream_t st, int64_t *n_alive) {
+  const int64_t n = ps->n;
+  if (n_alive) *n_alive = n;
+  if (n == 0) return cudaSuccess;
+  if (n >= (int64_t)0xFFFFFFFFll) return cudaErrorInvalidValue;
+  const pg_fieldset *fs = ps->fs;
+  const MortonSpec m = morton_spec(fs, n);
+  const uint32_t dead = 1u << m.total;
+  const int64_t nb = (int64_t)dead + 1;
+  cudaError_t e;
+  if ((e = prepare_resort(ps)) != cudaSuccess) return e;
   uint32_t *key = (uint32_t *)ps->sort_scratch;
   uint32_t *perm = key + n;
   uint32_t *count = perm + n;
@@ -242,7 +263,8 @@ cudaError_t launch_resort(pg_pset *ps, cudaStream_t st, int64_t *n_alive) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = exclusive_scan(count, offset, nb, tmp, st)) != cudaSuccess) return e;
   uint32_t dead_count = 0;
-  if ((e = cudaMemcpyAsync(&dead_count, count + dead, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+  if (n_alive &&
+      (e = cudaMemcpyAsync(&dead_count, count + dead, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return e;
   scatter_kernel<<<gr, 256, 0, st>>>(key, offset, perm, n);
   PsetArrays &B = ps->alt;
@@ -268,6 +290,23 @@ cudaError_t launch_resort(pg_pset *ps, cudaStream_t st, int64_t *n_alive) {
   gather_kernel<uint8_t><<<gr, 256, 0, st>>>(ps->status, B.status, perm, n);
   note_launches(ps->pos == PG_POS_CELL ? 11 : 8);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (!n_alive) {
+    // fixed-pointer mode: copy the sorted arrays back in place
+    const auto arrays_a = std::vector<std::pair<void *, void *>>{
+        {ps->x, B.x}, {ps->y, B.y}, {ps->z, B.z}, {ps->ci, B.ci}, {ps->cj, B.cj},
+        {ps->ck, B.ck}, {ps->fx, B.fx}, {ps->fy, B.fy}, {ps->fz, B.fz}};
+    const size_t el = ps->pos == PG_POS_F64 ? 8 : 4;
+    for (const auto &pr : arrays_a)
+      if (pr.first && (e = cudaMemcpyAsync(pr.first, pr.second, (size_t)n * el,
+                                           cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(ps->time, B.time, (size_t)n * 8, cudaMemcpyDeviceToDevice, st)) ||
+        (e = cudaMemcpyAsync(ps->id, B.id, (size_t)n * 8, cudaMemcpyDeviceToDevice, st)) ||
+        (e = cudaMemcpyAsync(ps->step, B.step, (size_t)n * 4, cudaMemcpyDeviceToDevice, st)) ||
+        (e = cudaMemcpyAsync(ps->status, B.status, (size_t)n, cudaMemcpyDeviceToDevice, st)))
+      return e;
+    return cudaSuccess;
+  }
   // swap the two array sets
   PsetArrays A;
   A.x = ps->x; A.y = ps->y; A.z = ps->z; A.ci = ps->ci; A.cj = ps->cj; A.ck = ps->ck;
