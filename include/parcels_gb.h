@@ -251,6 +251,37 @@ PG_API pg_status pg_execute_batch(int nrel, pg_pset *const *psets, const pg_kern
                                   const pg_tune *tune, pg_tune *chosen, const char *tune_cache,
                                   int use_graph, void *stream, int64_t *steps_done);
 
+/* ------------------------------------------------- flow-map surrogate MLP */
+
+/* A multilayer perceptron n_in -> width (x depth hidden layers, GELU) ->
+ * n_out for the learned 24-hour flow map (not part of the paper's method; a
+ * surrogate judged and backed by the RK4 of Sect. 2.1.1).  Weights are BF16
+ * copies of FP32 master parameters; every matrix product runs on the tensor
+ * cores with FP32 accumulation.  Widths are padded to multiples of 64 with
+ * zeros.  He-uniform initialisation from `seed`. */
+typedef struct pg_mlp pg_mlp;
+PG_API pg_status pg_mlp_create(int n_in, int width, int depth, int n_out, uint64_t seed,
+                               pg_mlp **out);
+PG_API pg_status pg_mlp_destroy(pg_mlp *net);
+/* Parameter counts: padded layout and the real (unpadded) network. */
+PG_API pg_status pg_mlp_num_params(const pg_mlp *net, int64_t *padded, int64_t *real);
+/* FP32 parameters in the padded layout, host memory: for each layer l, W_l
+ * [dout x din] row-major then b_l [dout]; din/dout are the padded widths. */
+PG_API pg_status pg_mlp_get_params(const pg_mlp *net, float *host);
+PG_API pg_status pg_mlp_set_params(pg_mlp *net, const float *host);
+/* Forward products on tcgen05 (1) or warp-level mma.sync (0, default). */
+PG_API pg_status pg_mlp_set_engine(pg_mlp *net, int tcgen05);
+/* y [M x n_out] = net(x [M x n_in]); device FP32 arrays, on `stream`. */
+PG_API pg_status pg_mlp_forward(pg_mlp *net, const float *x, int64_t M, float *y, void *stream);
+/* Gradient of L = 0.5 mean_rows sum_out (y - t)^2 for a batch (device x, t;
+ * M a multiple of 32); loss to *loss, gradients (padded layout) to host
+ * `grad` if non-NULL. */
+PG_API pg_status pg_mlp_grad(pg_mlp *net, const float *x, const float *t, int64_t M, float *loss,
+                             float *grad, void *stream);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) on a batch. */
+PG_API pg_status pg_mlp_train_step(pg_mlp *net, const float *x, const float *t, int64_t M,
+                                   float lr, float *loss, void *stream);
+
 /* Morton re-sort now: order particles by the Morton code of their cell
  * indices and move deleted particles behind the alive ones. */
 PG_API pg_status pg_pset_resort(pg_pset *ps, void *stream);

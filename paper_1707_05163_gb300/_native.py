@@ -82,6 +82,15 @@ _SIGS = {
     "pg_moments_f64_noalloc": ([_P, _P, _P, _P, C.c_int64, _P, _P], C.c_int),
     "pg_execute_batch": ([C.c_int, _P, _P, _P, _P, C.c_double, C.POINTER(Tune), C.POINTER(Tune),
                           C.c_char_p, C.c_int, _P, C.POINTER(C.c_int64)], C.c_int),
+    "pg_mlp_create": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(_P)], C.c_int),
+    "pg_mlp_destroy": ([_P], C.c_int),
+    "pg_mlp_num_params": ([_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
+    "pg_mlp_get_params": ([_P, _P], C.c_int),
+    "pg_mlp_set_params": ([_P, _P], C.c_int),
+    "pg_mlp_set_engine": ([_P, C.c_int], C.c_int),
+    "pg_mlp_forward": ([_P, _P, C.c_int64, _P, _P], C.c_int),
+    "pg_mlp_grad": ([_P, _P, _P, C.c_int64, C.POINTER(C.c_float), _P, _P], C.c_int),
+    "pg_mlp_train_step": ([_P, _P, _P, C.c_int64, C.c_float, C.POINTER(C.c_float), _P], C.c_int),
 }
 
 _lock = threading.Lock()

@@ -341,3 +341,63 @@ def execute_batch(psets, kernels, runtimes, dts, window=86400.0, tune=None, tune
                                  str(tune_cache).encode() if tune_cache else None,
                                  int(bool(use_graph)), _stream(stream), C.byref(steps)))
     return steps.value, (chosen.block, chosen.resort_steps)
+
+
+class MLP:
+    """The surrogate network (pg_mlp_*): BF16 tensor-core products, FP32 masters."""
+
+    def __init__(self, n_in=37, width=256, depth=4, n_out=3, seed=0):
+        self._lib = N.load()
+        self.n_in, self.width, self.depth, self.n_out = n_in, width, depth, n_out
+        h = C.c_void_p()
+        N.check(self._lib.pg_mlp_create(n_in, width, depth, n_out, int(seed), C.byref(h)))
+        self.h = h
+
+    def num_params(self):
+        p, r = C.c_int64(), C.c_int64()
+        N.check(self._lib.pg_mlp_num_params(self.h, C.byref(p), C.byref(r)))
+        return p.value, r.value
+
+    def get_params(self):
+        out = np.empty(self.num_params()[0], dtype=np.float32)
+        N.check(self._lib.pg_mlp_get_params(self.h, out.ctypes.data))
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.num_params()[0]
+        N.check(self._lib.pg_mlp_set_params(self.h, flat.ctypes.data))
+
+    def set_engine(self, tcgen05):
+        N.check(self._lib.pg_mlp_set_engine(self.h, int(bool(tcgen05))))
+
+    def forward(self, x, out=None, stream=None):
+        """x: CUDA float32 tensor [M x n_in] -> CUDA float32 tensor [M x n_out]."""
+        import torch
+        x = x.contiguous()
+        M = x.shape[0]
+        if out is None:
+            out = torch.empty((M, self.n_out), dtype=torch.float32, device=x.device)
+        N.check(self._lib.pg_mlp_forward(self.h, x.data_ptr(), M, out.data_ptr(), _stream(stream)))
+        return out
+
+    def grad(self, x, t, stream=None):
+        loss = C.c_float()
+        g = np.empty(self.num_params()[0], dtype=np.float32)
+        N.check(self._lib.pg_mlp_grad(self.h, x.contiguous().data_ptr(), t.contiguous().data_ptr(),
+                                      x.shape[0], C.byref(loss), g.ctypes.data, _stream(stream)))
+        return loss.value, g
+
+    def train_step(self, x, t, lr, stream=None):
+        loss = C.c_float()
+        N.check(self._lib.pg_mlp_train_step(self.h, x.data_ptr(), t.data_ptr(), x.shape[0],
+                                            float(lr), C.byref(loss), _stream(stream)))
+        return loss.value
+
+    def __del__(self):
+        try:
+            if self.h:
+                self._lib.pg_mlp_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass

@@ -29,6 +29,8 @@ UNITS = {
     "advect_cell.cu": [],
     "moments_noalloc.cu": [],
     "batch.cu": [],
+    "mlp.cu": [],
+    "mlp_tc.cu": [],
     "advect_f32.cu": ([f"-maxrregcount={os.environ['PG_MAXRREG']}"]
                       if os.environ.get("PG_MAXRREG") else []),
 }

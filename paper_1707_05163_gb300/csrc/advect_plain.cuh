@@ -263,32 +263,35 @@ struct BatchArgs {
   int *err;
 };
 
+// The argument block of the current tile's release is assembled once per
+// tile in shared memory, which every thread of the tile then reads.
 template <typename Store, int NF, bool D3>
 __global__ void __launch_bounds__(256, 2) advect_batch_kernel(BatchArgs b) {
   __shared__ int tile;
+  __shared__ StepArgs sa;
   unsigned long long done = 0;
   for (;;) {
-    if (threadIdx.x == 0) tile = atomicAdd(b.next_tile, 1);
+    if (threadIdx.x == 0) {
+      tile = atomicAdd(b.next_tile, 1);
+      if (tile < b.ntiles) {
+        const BatchRelease *R = b.rel + b.tiles[tile].x;
+        sa.g = b.g;
+        sa.f = b.f;
+        sa.k = R->k;
+        sa.p = R->p;
+        sa.dt = R->dt;
+        sa.t_stop = b.t_stop;
+        sa.t_end = R->t_end;
+        sa.steps_done = b.steps_done;
+        sa.err = b.err;
+      }
+    }
     __syncthreads();
     const int t = tile;
-    __syncthreads();
     if (t >= b.ntiles) break;
-    const int2 td = b.tiles[t];
-    const BatchRelease *R = b.rel + td.x;
-    const int64_t p = (int64_t)td.y + threadIdx.x;
-    if (p < R->p.n && R->p.status[p] == 0) {
-      StepArgs a;
-      a.g = b.g;
-      a.f = b.f;
-      a.k = R->k;
-      a.p = R->p;
-      a.dt = R->dt;
-      a.t_stop = b.t_stop;
-      a.t_end = R->t_end;
-      a.steps_done = b.steps_done;
-      a.err = b.err;
-      done += advance_particle<float, Store, NF, D3>(a, p);
-    }
+    const int64_t p = (int64_t)b.tiles[t].y + threadIdx.x;
+    if (p < sa.p.n && sa.p.status[p] == 0) done += advance_particle<float, Store, NF, D3>(sa, p);
+    __syncthreads();
   }
   count_steps(done, b.steps_done);
 }
