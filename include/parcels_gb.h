@@ -282,6 +282,43 @@ PG_API pg_status pg_mlp_grad(pg_mlp *net, const float *x, const float *t, int64_
 PG_API pg_status pg_mlp_train_step(pg_mlp *net, const float *x, const float *t, int64_t M,
                                    float lr, float *loss, void *stream);
 
+/* Surrogate inputs of every particle of a set (FP32 positions on a resident
+ * FP32 field set) at its current time, 37 floats per particle into device
+ * x[n x 37]: the position inside its lon and lat cell (0..1), lat / 90,
+ * depth / 1000 m, the phase of the field's period (0..1), then U and V
+ * divided by 0.3 m/s at the 4 x 4 nodes i-1..i+2, j-1..j+2 around the cell,
+ * interpolated linearly in depth and time to the particle.  Deleted
+ * particles get zeros. */
+PG_API pg_status pg_surrogate_features(const pg_pset *ps, float *x, void *stream);
+/* Move every alive particle by y[n x 3] (device): cells of lon and lat and
+ * units of 100 m of depth; time advances by `horizon` seconds.  Positions
+ * leaving the domain delete the particle (status as for advection). */
+PG_API pg_status pg_surrogate_apply(pg_pset *ps, const float *y, double horizon, void *stream);
+/* Displacement of each particle from set a to set b (same particles in the
+ * same order) in the units of pg_surrogate_apply, into device y[n x 3]. */
+PG_API pg_status pg_pset_displacement(const pg_pset *a, const pg_pset *b, float *y, void *stream);
+
+typedef struct {
+    int64_t network_steps;      /* particle x network steps taken                     */
+    int64_t checked;            /* particle checks where both kept the particle alive */
+    int64_t rejected;           /* particles re-integrated with RK4                   */
+    int64_t rk4_particle_steps; /* RK4 particle-steps spent on checks and fallback    */
+    double error_sum;           /* sum of checked errors in cells                     */
+    double seconds_network;     /* device time of the network steps                   */
+    double seconds_rk4;         /* device time of checks and fallback                 */
+    double seconds_total;       /* wall time of the call                              */
+} pg_surrogate_stats;
+
+/* Surrogate run: `nsteps` network steps of `horizon` seconds in blocks of
+ * `check_every`.  The last step of every block is judged by RK4 with steps of
+ * dt_check from the same state: particles whose position differs by more than
+ * `threshold` cells (depth: layers), or whose status differs, are
+ * re-integrated with RK4 from the start of the block; all others take RK4's
+ * state for the judged step.  The kernel `k` is the RK4 of the judge. */
+PG_API pg_status pg_surrogate_run(pg_pset *ps, pg_mlp *net, const pg_kernel *k, int nsteps,
+                                  int check_every, double horizon, double dt_check,
+                                  double threshold, pg_surrogate_stats *stats, void *stream);
+
 /* Morton re-sort now: order particles by the Morton code of their cell
  * indices and move deleted particles behind the alive ones. */
 PG_API pg_status pg_pset_resort(pg_pset *ps, void *stream);

@@ -44,6 +44,13 @@ class Tune(C.Structure):
     _fields_ = [("block", C.c_int), ("resort_steps", C.c_int), ("chunk_steps", C.c_int)]
 
 
+class SurrogateStats(C.Structure):
+    _fields_ = [("network_steps", C.c_int64), ("checked", C.c_int64), ("rejected", C.c_int64),
+                ("rk4_particle_steps", C.c_int64), ("error_sum", C.c_double),
+                ("seconds_network", C.c_double), ("seconds_rk4", C.c_double),
+                ("seconds_total", C.c_double)]
+
+
 SNAPSHOT_CB = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_size_t)
 OUTPUT_CB = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_double, C.c_int64, C.c_void_p, C.c_void_p,
                         C.c_void_p, C.c_void_p, C.c_void_p)
@@ -82,6 +89,11 @@ _SIGS = {
     "pg_moments_f64_noalloc": ([_P, _P, _P, _P, C.c_int64, _P, _P], C.c_int),
     "pg_execute_batch": ([C.c_int, _P, _P, _P, _P, C.c_double, C.POINTER(Tune), C.POINTER(Tune),
                           C.c_char_p, C.c_int, _P, C.POINTER(C.c_int64)], C.c_int),
+    "pg_surrogate_features": ([_P, _P, _P], C.c_int),
+    "pg_surrogate_apply": ([_P, _P, C.c_double, _P], C.c_int),
+    "pg_pset_displacement": ([_P, _P, _P, _P], C.c_int),
+    "pg_surrogate_run": ([_P, _P, _P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                          C.POINTER(SurrogateStats), _P], C.c_int),
     "pg_mlp_create": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(_P)], C.c_int),
     "pg_mlp_destroy": ([_P], C.c_int),
     "pg_mlp_num_params": ([_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),

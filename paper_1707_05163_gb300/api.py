@@ -401,3 +401,41 @@ class MLP:
                 self.h = None
         except Exception:
             pass
+
+
+N_FEATURES = 37
+
+
+def surrogate_features(pset, out=None, stream=None):
+    """Inputs of the surrogate for every particle (CUDA float32 [n x 37])."""
+    import torch
+    n = len(pset)
+    if out is None:
+        out = torch.empty((n, N_FEATURES), dtype=torch.float32, device="cuda")
+    N.check(N.load().pg_surrogate_features(pset.h, out.data_ptr(), _stream(stream)))
+    return out
+
+
+def surrogate_apply(pset, y, horizon, stream=None):
+    N.check(N.load().pg_surrogate_apply(pset.h, y.contiguous().data_ptr(), float(horizon),
+                                        _stream(stream)))
+
+
+def displacement(a, b, out=None, stream=None):
+    """Displacement from set a to set b (cells of lon/lat, 100 m of depth)."""
+    import torch
+    n = len(a)
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    N.check(N.load().pg_pset_displacement(a.h, b.h, out.data_ptr(), _stream(stream)))
+    return out
+
+
+def surrogate_run(pset, net, kernel, nsteps, check_every=5, horizon=86400.0, dt_check=1800.0,
+                  threshold=1e-3, stream=None):
+    """Network steps with periodic RK4 checks and fallback; returns the stats dict."""
+    s = N.SurrogateStats()
+    N.check(N.load().pg_surrogate_run(pset.h, net.h, kernel.h, int(nsteps), int(check_every),
+                                      float(horizon), float(dt_check), float(threshold),
+                                      C.byref(s), _stream(stream)))
+    return {k: getattr(s, k) for k, _ in N.SurrogateStats._fields_}

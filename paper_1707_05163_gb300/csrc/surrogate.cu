@@ -1,0 +1,484 @@
+// surrogate.cu -- the learned 24-hour flow map: features, displacement,
+// and the run loop in which RK4 (Sect. 2.1.1) checks the network and takes
+// over for the particles it rejects.
+//
+// Features of a particle at time t (37 floats):
+//   0 xi, 1 eta       position inside its lon / lat cell, in [0, 1]
+//   2 lat / 90, 3 depth / 1000 m, 4 phase of the field's period in [0, 1)
+//   5..36             U and V / 0.3 m/s at the 4 x 4 nodes around the cell
+//                     (i-1..i+2, j-1..j+2), interpolated linearly in depth
+//                     and in time to the particle's depth and time
+// Output (3 floats): displacement over the horizon in cells of lon and lat,
+// and in units of 100 m of depth.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "advect_common.cuh"
+#include "pg_host.h"
+
+namespace pg {
+
+namespace {
+
+constexpr int kFeat = 37;
+constexpr float kVelScale = 1.0f / 0.3f;
+constexpr float kDepthUnit = 100.0f;
+
+__device__ __forceinline__ int find_cell(const float *x, int n, float p) {
+  int lo = 0, hi = n - 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (x[mid] <= p) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void features_kernel(GridArgs g, FieldArgs f, const float *lon, const float *lat,
+                                const float *dep, const double *time, const uint8_t *status,
+                                int64_t n, float *out, int *err) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    float *o = out + p * kFeat;
+    if (status[p] != 0) {
+      for (int q = 0; q < kFeat; ++q) o[q] = 0.f;
+      continue;
+    }
+    // cell and fractions
+    float q = wrap_lon(lon[p], g.lonf[0]);
+    int i;
+    float xi;
+    if (q >= g.lonf[g.nx - 1]) {
+      i = g.nx - 1;
+      xi = (q - g.lonf[g.nx - 1]) / (g.lon_end_f - g.lonf[g.nx - 1]);
+    } else {
+      i = find_cell(g.lonf, g.nx, q);
+      xi = (q - g.lonf[i]) / (g.lonf[i + 1] - g.lonf[i]);
+    }
+    const float y = fminf(fmaxf(lat[p], g.latf[0]), g.latf[g.ny - 1]);
+    const int j = find_cell(g.latf, g.ny, y);
+    const float eta = (y - g.latf[j]) / (g.latf[j + 1] - g.latf[j]);
+    int k = 0;
+    float zeta = 0.f;
+    if (g.nz > 1) {
+      const float z = fminf(fmaxf(dep[p], g.depthf[0]), g.depthf[g.nz - 1]);
+      k = find_cell(g.depthf, g.nz, z);
+      zeta = (z - g.depthf[k]) / (g.depthf[k + 1] - g.depthf[k]);
+    }
+    // time interval
+    int s0 = 0, s1 = 0;
+    float tau = 0.f, phase = 0.f;
+    if (f.nt > 1) {
+      double tt, ta, tb;
+      int a0 = -1, a1 = -1;
+      if (!time_interval(f, time[p], a0, a1, tt, ta, tb)) {
+        atomicCAS(err, 0, (int)DEVERR_TIME_RANGE);
+        continue;
+      }
+      s0 = a0; s1 = a1;
+      tau = (float)((tt - ta) / (tb - ta));
+      if (f.period > 0.0) phase = (float)((tt - f.times[0]) / f.period);
+    }
+    const float *S0 = reinterpret_cast<const float *>(f.tab[s0]);
+    const float *S1 = reinterpret_cast<const float *>(f.tab[s1]);
+    if (!S0 || !S1) {
+      atomicCAS(err, 0, (int)DEVERR_SLAB_MISSING);
+      continue;
+    }
+    const int stride = f.nf == 2 ? 2 : 4;
+    o[0] = xi; o[1] = eta; o[2] = lat[p] * (1.0f / 90.0f); o[3] = dep[p] * 1e-3f; o[4] = phase;
+    int q2 = 5;
+    for (int dj = -1; dj <= 2; ++dj) {
+      const int jj = min(max(j + dj, 0), g.ny - 1);
+      for (int di = -1; di <= 2; ++di) {
+        int ii = i + di;
+        if (ii < 0) ii += g.nx;
+        if (ii >= g.nx) ii -= g.nx;
+        float uv[2];
+        for (int c = 0; c < 2; ++c) {
+          const size_t n0 = (((size_t)k * g.ny + jj) * g.nx + ii) * stride + c;
+          const size_t n1 = g.nz > 1 ? n0 + (size_t)g.ny * g.nx * stride : n0;
+          const float a = S0[n0] + (S0[n1] - S0[n0]) * zeta;
+          const float b = S1[n0] + (S1[n1] - S1[n0]) * zeta;
+          uv[c] = (a + (b - a) * tau) * kVelScale;
+        }
+        o[q2++] = uv[0];
+        o[q2++] = uv[1];
+      }
+    }
+  }
+}
+
+// Apply predicted displacements over `horizon` seconds.
+__global__ void apply_kernel(GridArgs g, float *lon, float *lat, float *dep, double *time,
+                             uint32_t *step, uint8_t *status, int64_t n, const float *y,
+                             double horizon) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    if (status[p] != 0) continue;
+    float nl = lon[p] + y[p * 3 + 0] * g.df[0];
+    const float na = lat[p] + y[p * 3 + 1] * g.df[1];
+    const float nd = dep[p] + y[p * 3 + 2] * kDepthUnit;
+    if (g.periodic) nl = wrap_lon(nl, g.lonf[0]);
+    uint8_t st = 0;
+    if (!g.periodic && !(nl >= g.lonf[0] && nl <= g.lonf[g.nx - 1])) st = 1;
+    else if (!(na >= g.latf[0] && na <= g.latf[g.ny - 1])) st = 1;
+    else if (g.nz > 1 && !(nd >= g.depthf[0] && nd <= g.depthf[g.nz - 1])) st = 2;
+    else if (!(nl == nl)) st = 3;
+    if (st) { status[p] = st; continue; }
+    lon[p] = nl; lat[p] = na; dep[p] = nd;
+    time[p] += horizon;
+    step[p] += 1;
+  }
+}
+
+// Displacement between two states of the same particles (same order):
+// cells of lon (shortest way round) and lat, 100 m units of depth.
+__global__ void displacement_kernel(GridArgs g, const float *lon0, const float *lat0,
+                                    const float *dep0, const float *lon1, const float *lat1,
+                                    const float *dep1, int64_t n, float *y) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    float dl = lon1[p] - lon0[p];
+    if (g.periodic) {
+      if (dl > 180.f) dl -= 360.f;
+      if (dl < -180.f) dl += 360.f;
+    }
+    y[p * 3 + 0] = dl / g.df[0];
+    y[p * 3 + 1] = (lat1[p] - lat0[p]) / g.df[1];
+    y[p * 3 + 2] = (dep1[p] - dep0[p]) / kDepthUnit;
+  }
+}
+
+// Position error (in cells; depth in units of the local layer) between the
+// network's state and RK4's; rejects particles above the threshold or whose
+// status differs.  err_sum[0] += error over particles both keep alive,
+// err_sum[1] += count.
+__global__ void check_kernel(GridArgs g, const float *lon_a, const float *lat_a,
+                             const float *dep_a, const uint8_t *st_a, const float *lon_b,
+                             const float *lat_b, const float *dep_b, const uint8_t *st_b,
+                             int64_t n, float threshold, uint8_t *reject, double *err_sum,
+                             unsigned long long *n_reject) {
+  double e_acc = 0.0, c_acc = 0.0;
+  unsigned long long r_acc = 0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    uint8_t rj = 0;
+    if (st_a[p] != st_b[p]) {
+      rj = 1;
+    } else if (st_b[p] == 0) {
+      float dl = lon_a[p] - lon_b[p];
+      if (g.periodic) {
+        if (dl > 180.f) dl -= 360.f;
+        if (dl < -180.f) dl += 360.f;
+      }
+      float e = fmaxf(fabsf(dl) / g.df[0], fabsf(lat_a[p] - lat_b[p]) / g.df[1]);
+      if (g.nz > 1) {
+        const int k = find_cell(g.depthf, g.nz, fminf(fmaxf(dep_b[p], g.depthf[0]), g.depthf[g.nz - 1]));
+        e = fmaxf(e, fabsf(dep_a[p] - dep_b[p]) / (g.depthf[k + 1] - g.depthf[k]));
+      }
+      if (!(e <= threshold)) rj = 1;
+      e_acc += (double)fminf(e, 1e6f);
+      c_acc += 1.0;
+    }
+    reject[p] = rj;
+    r_acc += rj;
+  }
+  atomicAdd(&err_sum[0], e_acc);
+  atomicAdd(&err_sum[1], c_acc);
+  atomicAdd(n_reject, r_acc);
+}
+
+// Accepted particles are parked (status 255, skipped by the advection
+// kernels) while the rejected ones, restored from the checkpoint, are
+// re-integrated; unpark turns 255 back into alive.
+__global__ void park_kernel(uint8_t *status, const uint8_t *reject, int64_t n) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x)
+    if (!reject[p] && status[p] == 0) status[p] = 255;
+}
+__global__ void unpark_kernel(uint8_t *status, int64_t n) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x)
+    if (status[p] == 255) status[p] = 0;
+}
+// rejected particles take the checkpoint state
+template <typename T>
+__global__ void select_kernel(T *dst, const T *ckpt, const uint8_t *reject, int64_t n) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x)
+    if (reject[p]) dst[p] = ckpt[p];
+}
+
+int grid_of(int64_t n, int sm) {
+  int64_t g = (n + 255) / 256;
+  if (g > (int64_t)sm * 16) g = (int64_t)sm * 16;
+  return (int)(g < 1 ? 1 : g);
+}
+
+FieldArgs field_args(const pg_fieldset *fs) {
+  FieldArgs f;
+  f.nt = fs->nt; f.nf = fs->nfields; f.times = fs->d_times; f.period = fs->period;
+  f.tab = fs->d_tab;
+  f.scales = nullptr;
+  return f;
+}
+
+}  // namespace
+
+}  // namespace pg
+
+using namespace pg;
+
+#define CUS(call)                                                                     \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      set_error("%s failed: %s", #call, cudaGetErrorString(e_));                      \
+      return e_ == cudaErrorMemoryAllocation ? PG_ERR_NOMEM : PG_ERR_CUDA;            \
+    }                                                                                 \
+  } while (0)
+
+static pg_status check_pset(const pg_pset *ps) {
+  if (!ps) {
+    set_error("invalid argument: null particle set");
+    return PG_ERR_ARG;
+  }
+  if (ps->pos != PG_POS_F32 || ps->fs->storage != PG_F32 || ps->fs->streaming) {
+    set_error("the surrogate needs FP32 positions on a resident FP32 field set");
+    return PG_ERR_UNSUPPORTED;
+  }
+  return PG_OK;
+}
+
+extern "C" {
+
+pg_status pg_surrogate_features(const pg_pset *ps, float *x, void *stream) {
+  clear_error();
+  pg_status r = check_pset(ps);
+  if (r) return r;
+  if (!x && ps->n) { set_error("invalid argument: null output"); return PG_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ps->n == 0) return PG_OK;
+  CUS(cudaMemsetAsync(ps->d_err, 0, 4, st));
+  features_kernel<<<grid_of(ps->n, ps->fs->sm_count), 256, 0, st>>>(
+      grid_args_of(ps->fs), field_args(ps->fs), (const float *)ps->x, (const float *)ps->y,
+      (const float *)ps->z, ps->time, ps->status, ps->n, x, ps->d_err);
+  note_launches(1);
+  CUS(cudaGetLastError());
+  int err = 0;
+  CUS(cudaMemcpyAsync(&err, ps->d_err, 4, cudaMemcpyDeviceToHost, st));
+  CUS(cudaStreamSynchronize(st));
+  if (err) { set_error("feature kernel recorded internal error %d", err); return PG_ERR_DEVICE; }
+  return PG_OK;
+}
+
+pg_status pg_surrogate_apply(pg_pset *ps, const float *y, double horizon, void *stream) {
+  clear_error();
+  pg_status r = check_pset(ps);
+  if (r) return r;
+  if ((!y && ps->n) || !std::isfinite(horizon)) { set_error("invalid argument"); return PG_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ps->n) {
+    apply_kernel<<<grid_of(ps->n, ps->fs->sm_count), 256, 0, st>>>(
+        grid_args_of(ps->fs), (float *)ps->x, (float *)ps->y, (float *)ps->z, ps->time, ps->step,
+        ps->status, ps->n, y, horizon);
+    note_launches(1);
+    CUS(cudaGetLastError());
+  }
+  ps->t_min += horizon;
+  ps->t_max += horizon;
+  return PG_OK;
+}
+
+pg_status pg_pset_displacement(const pg_pset *a, const pg_pset *b, float *y, void *stream) {
+  clear_error();
+  pg_status r = check_pset(a);
+  if (!r) r = check_pset(b);
+  if (r) return r;
+  if (a->n != b->n || a->fs != b->fs || (!y && a->n)) {
+    set_error("invalid argument: sets of equal size on one field set and an output");
+    return PG_ERR_ARG;
+  }
+  if (a->n == 0) return PG_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  displacement_kernel<<<grid_of(a->n, a->fs->sm_count), 256, 0, st>>>(
+      grid_args_of(a->fs), (const float *)a->x, (const float *)a->y, (const float *)a->z,
+      (const float *)b->x, (const float *)b->y, (const float *)b->z, a->n, y);
+  note_launches(1);
+  CUS(cudaGetLastError());
+  return PG_OK;
+}
+
+pg_status pg_mlp_forward(pg_mlp *net, const float *x, int64_t M, float *y, void *stream);
+
+// The surrogate run: blocks of `check_every` network steps of `horizon`
+// seconds.  The last step of every block is judged by RK4 (dt_check) from
+// the same state; particles whose error exceeds `threshold` cells (or whose
+// status differs) are re-integrated with RK4 from the block's start, the
+// others take RK4's state for that step.
+pg_status pg_surrogate_run(pg_pset *ps, pg_mlp *net, const pg_kernel *k, int nsteps,
+                           int check_every, double horizon, double dt_check, double threshold,
+                           pg_surrogate_stats *stats, void *stream) {
+  clear_error();
+  pg_status r = check_pset(ps);
+  if (r) return r;
+  if (!net || !k || nsteps < 1 || check_every < 1 || !(horizon > 0.0) || !(dt_check > 0.0) ||
+      !(threshold >= 0.0)) {
+    set_error("invalid argument: need a network, a kernel, nsteps, check_every >= 1, horizon, "
+              "dt_check > 0 and threshold >= 0");
+    return PG_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = ps->n;
+  const int sm = ps->fs->sm_count;
+  pg_surrogate_stats S{};
+  // buffers: features, outputs, reject flags, checkpoint and check sets
+  float *x = nullptr, *y = nullptr;
+  uint8_t *rej = nullptr;
+  double *esum = nullptr;
+  unsigned long long *nrej = nullptr;
+  pg_pset *ckpt = nullptr, *chk = nullptr;
+  cudaEvent_t e0, e1, e2;
+  CUS(cudaEventCreate(&e0));
+  CUS(cudaEventCreate(&e1));
+  CUS(cudaEventCreate(&e2));
+  auto cleanup = [&]() {
+    dev_free(x); dev_free(y); dev_free(rej); dev_free(esum); dev_free(nrej);
+    if (ckpt) pg_pset_destroy(ckpt);
+    if (chk) pg_pset_destroy(chk);
+    cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
+  };
+  cudaError_t e = dev_alloc((void **)&x, (size_t)std::max<int64_t>(n, 1) * kFeat * 4);
+  if (e == cudaSuccess) e = dev_alloc((void **)&y, (size_t)std::max<int64_t>(n, 1) * 3 * 4);
+  if (e == cudaSuccess) e = dev_alloc((void **)&rej, (size_t)std::max<int64_t>(n, 1));
+  if (e == cudaSuccess) e = dev_alloc((void **)&esum, 16);
+  if (e == cudaSuccess) e = dev_alloc((void **)&nrej, 8);
+  if (e != cudaSuccess) {
+    cleanup();
+    set_error("surrogate buffers: %s", cudaGetErrorString(e));
+    return PG_ERR_NOMEM;
+  }
+  // two more sets with the same arrays' shapes
+  std::vector<double> zeros(1, 0.0);
+  if ((r = pg_pset_create(ps->fs, 0, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr, 0,
+                          PG_POS_F32, ps->seed, &ckpt)) ||
+      (r = pg_pset_create(ps->fs, 0, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr, 0,
+                          PG_POS_F32, ps->seed, &chk))) {
+    cleanup();
+    return r;
+  }
+  auto copy_set = [&](pg_pset *dst, const pg_pset *src) -> cudaError_t {
+    if (dst->cap < src->n) {
+      PsetArrays A;
+      if (alloc_arrays(A, PG_POS_F32, src->n) != PG_OK) return cudaErrorMemoryAllocation;
+      PsetArrays old;
+      old.x = dst->x; old.y = dst->y; old.z = dst->z; old.time = dst->time; old.id = dst->id;
+      old.step = dst->step; old.status = dst->status;
+      old.free_all();
+      dst->x = A.x; dst->y = A.y; dst->z = A.z; dst->time = A.time; dst->id = A.id;
+      dst->step = A.step; dst->status = A.status;
+      dst->cap = src->n;
+    }
+    const size_t m = (size_t)src->n;
+    cudaError_t q = cudaMemcpyAsync(dst->x, src->x, m * 4, cudaMemcpyDeviceToDevice, st);
+    if (!q) q = cudaMemcpyAsync(dst->y, src->y, m * 4, cudaMemcpyDeviceToDevice, st);
+    if (!q) q = cudaMemcpyAsync(dst->z, src->z, m * 4, cudaMemcpyDeviceToDevice, st);
+    if (!q) q = cudaMemcpyAsync(dst->time, src->time, m * 8, cudaMemcpyDeviceToDevice, st);
+    if (!q) q = cudaMemcpyAsync(dst->id, src->id, m * 8, cudaMemcpyDeviceToDevice, st);
+    if (!q) q = cudaMemcpyAsync(dst->step, src->step, m * 4, cudaMemcpyDeviceToDevice, st);
+    if (!q) q = cudaMemcpyAsync(dst->status, src->status, m, cudaMemcpyDeviceToDevice, st);
+    dst->n = src->n;
+    dst->t_min = src->t_min;
+    dst->t_max = src->t_max;
+    return q;
+  };
+  auto network_step = [&]() -> pg_status {
+    pg_status q = pg_surrogate_features(ps, x, st);
+    if (!q) q = pg_mlp_forward(net, x, n, y, st);
+    if (!q) q = pg_surrogate_apply(ps, y, horizon, st);
+    return q;
+  };
+  pg_tune keep_order{ps->tune.block, 0, 0};
+  float ms_net = 0.f, ms_rk = 0.f;
+  const auto t_start = std::chrono::steady_clock::now();
+  int done_steps = 0;
+  while (done_steps < nsteps && r == PG_OK) {
+    const int blk = std::min(check_every, nsteps - done_steps);
+    e = copy_set(ckpt, ps);
+    if (e) { r = PG_ERR_CUDA; set_error("checkpoint copy: %s", cudaGetErrorString(e)); break; }
+    cudaEventRecord(e0, st);
+    for (int s = 0; s < blk - 1 && r == PG_OK; ++s) r = network_step();
+    if (r) break;
+    // judge the last step of the block: RK4 on a copy, the network on ps
+    e = copy_set(chk, ps);
+    if (e) { r = PG_ERR_CUDA; set_error("check copy: %s", cudaGetErrorString(e)); break; }
+    if ((r = network_step())) break;
+    cudaEventRecord(e1, st);
+    chk->tune = keep_order;
+    int64_t rk = 0;
+    if ((r = pg_execute(chk, k, horizon, dt_check, 0.0, nullptr, nullptr, st, &rk))) break;
+    S.rk4_particle_steps += rk;
+    CUS(cudaMemsetAsync(esum, 0, 16, st));
+    CUS(cudaMemsetAsync(nrej, 0, 8, st));
+    check_kernel<<<grid_of(n, sm), 256, 0, st>>>(
+        grid_args_of(ps->fs), (const float *)ps->x, (const float *)ps->y, (const float *)ps->z,
+        ps->status, (const float *)chk->x, (const float *)chk->y, (const float *)chk->z,
+        chk->status, n, (float)threshold, rej, esum, nrej);
+    note_launches(1);
+    double h_esum[2];
+    unsigned long long h_nrej = 0;
+    CUS(cudaMemcpyAsync(h_esum, esum, 16, cudaMemcpyDeviceToHost, st));
+    CUS(cudaMemcpyAsync(&h_nrej, nrej, 8, cudaMemcpyDeviceToHost, st));
+    CUS(cudaStreamSynchronize(st));
+    S.checked += (int64_t)h_esum[1];
+    S.error_sum += h_esum[0];
+    S.rejected += (int64_t)h_nrej;
+    // everyone takes RK4's state for the judged step ...
+    if ((e = copy_set(ps, chk))) { r = PG_ERR_CUDA; set_error("%s", cudaGetErrorString(e)); break; }
+    // ... and the rejected re-integrate the whole block from the checkpoint
+    if (h_nrej > 0) {
+      const int g = grid_of(n, sm);
+      select_kernel<float><<<g, 256, 0, st>>>((float *)ps->x, (const float *)ckpt->x, rej, n);
+      select_kernel<float><<<g, 256, 0, st>>>((float *)ps->y, (const float *)ckpt->y, rej, n);
+      select_kernel<float><<<g, 256, 0, st>>>((float *)ps->z, (const float *)ckpt->z, rej, n);
+      select_kernel<double><<<g, 256, 0, st>>>(ps->time, ckpt->time, rej, n);
+      select_kernel<uint32_t><<<g, 256, 0, st>>>(ps->step, ckpt->step, rej, n);
+      select_kernel<uint8_t><<<g, 256, 0, st>>>(ps->status, ckpt->status, rej, n);
+      park_kernel<<<g, 256, 0, st>>>(ps->status, rej, n);
+      note_launches(7);
+      const pg_tune saved = ps->tune;
+      ps->tune = keep_order;
+      const double tmin = ps->t_min, tmax = ps->t_max;
+      ps->t_min = ckpt->t_min;
+      ps->t_max = ckpt->t_max;
+      r = pg_execute(ps, k, blk * horizon, dt_check, 0.0, nullptr, nullptr, st, &rk);
+      ps->tune = saved;
+      ps->t_min = tmin;
+      ps->t_max = tmax;
+      unpark_kernel<<<g, 256, 0, st>>>(ps->status, n);
+      note_launches(1);
+      if (r) break;
+      S.rk4_particle_steps += rk;
+    }
+    cudaEventRecord(e2, st);
+    CUS(cudaEventSynchronize(e2));
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, e0, e1);
+    cudaEventElapsedTime(&b, e1, e2);
+    ms_net += a;
+    ms_rk += b;
+    S.network_steps += (int64_t)(blk - 1) * n + n;
+    done_steps += blk;
+  }
+  S.seconds_network = ms_net * 1e-3;
+  S.seconds_rk4 = ms_rk * 1e-3;
+  S.seconds_total =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  if (stats) *stats = S;
+  cleanup();
+  return r;
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+"""The flow-map surrogate: features, displacements, training, and the run in
+which RK4 judges the network and takes over for rejected particles."""
+import numpy as np
+import pytest
+
+import synth
+from tests.helpers import DAY, cell_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1707_05163_gb300 as pg
+    pg.load()
+    gf = synth.GlobalField(res_deg=2.0, nz=8, nt=6, seed=41, kmax=20, period=6 * DAY)
+    spec = gf.spec(materialise=True)
+    fs = pg.FieldSet.from_spec(spec, storage="f32")
+    return pg, torch, spec, fs
+
+
+def _features_numpy(spec, lon, lat, dep, t):
+    """The 37 inputs, recomputed in FP64 from the field arrays by indexing."""
+    nx, ny, nz = len(spec.lon), len(spec.lat), len(spec.depth)
+    out = np.zeros((len(lon), 37))
+    for p in range(len(lon)):
+        q = np.mod(lon[p] - spec.lon[0], 360.0) + spec.lon[0]
+        i = min(int(np.searchsorted(spec.lon, q, "right") - 1), nx - 1)
+        hi = spec.lon[i + 1] if i < nx - 1 else spec.lon[0] + 360.0
+        xi = (q - spec.lon[i]) / (hi - spec.lon[i])
+        j = min(int(np.searchsorted(spec.lat, lat[p], "right") - 1), ny - 2)
+        eta = (lat[p] - spec.lat[j]) / (spec.lat[j + 1] - spec.lat[j])
+        k = min(int(np.searchsorted(spec.depth, dep[p], "right") - 1), nz - 2)
+        zeta = (dep[p] - spec.depth[k]) / (spec.depth[k + 1] - spec.depth[k])
+        tt = np.mod(t, spec.period)
+        s0 = min(int(tt // (spec.period / spec.nt)), spec.nt - 1)
+        s1 = (s0 + 1) % spec.nt
+        tau = (tt - spec.times[s0]) / (spec.period / spec.nt)
+        out[p, :5] = [xi, eta, lat[p] / 90.0, dep[p] / 1000.0, tt / spec.period]
+        c = 5
+        for dj in range(-1, 3):
+            jj = min(max(j + dj, 0), ny - 1)
+            for di in range(-1, 3):
+                ii = (i + di) % nx
+                for f in range(2):
+                    a = spec.data[s0, f, k, jj, ii] * (1 - zeta) + spec.data[s0, f, k + 1, jj, ii] * zeta
+                    b = spec.data[s1, f, k, jj, ii] * (1 - zeta) + spec.data[s1, f, k + 1, jj, ii] * zeta
+                    out[p, c] = (a + (b - a) * tau) / 0.3
+                    c += 1
+    return out
+
+
+def test_features_match_direct_indexing(env):
+    pg, torch, spec, fs = env
+    lon, lat, dep = synth.uniform_particles(300, 2, (0, 360), (-70, 70), (10.0, 800.0),
+                                            dtype=np.float32)
+    t0 = 1.3 * DAY
+    ps = pg.ParticleSet(fs, lon, lat, dep, t0=t0, pos="f32")
+    x = pg.surrogate_features(ps).cpu().numpy()
+    ref = _features_numpy(spec, lon, lat, dep, t0)
+    np.testing.assert_allclose(x, ref, rtol=0, atol=2e-5)
+
+
+def test_displacement_apply_roundtrip(env):
+    pg, torch, spec, fs = env
+    lon, lat, dep = synth.uniform_particles(2000, 3, (0, 360), (-60, 60), (10.0, 800.0),
+                                            dtype=np.float32)
+    a = pg.ParticleSet(fs, lon, lat, dep, pos="f32")
+    b = pg.ParticleSet(fs, lon, lat, dep, pos="f32")
+    b.execute(pg.Kernel("rk4"), DAY, 1800.0)
+    y = pg.displacement(a, b)
+    pg.surrogate_apply(a, y, DAY)
+    ga, gb = a.get(), b.get()
+    ok = gb["status"] == 0
+    assert np.max(cell_error(ga, gb, spec)[ok]) < 1e-3
+    assert (ga["time"][ok] == DAY).all()
+
+
+def test_run_rejecting_everything_is_plain_rk4(env):
+    pg, torch, spec, fs = env
+    lon, lat, dep = synth.uniform_particles(3000, 4, (0, 360), (-60, 60), (10.0, 800.0),
+                                            dtype=np.float32)
+    net = pg.MLP(37, 64, 2, 3, seed=3)          # untrained: every check fails
+    a = pg.ParticleSet(fs, lon, lat, dep, pos="f32")
+    stats = pg.surrogate_run(a, net, pg.Kernel("rk4"), nsteps=6, check_every=3, threshold=0.0)
+    ref = pg.ParticleSet(fs, lon, lat, dep, pos="f32")
+    ref.execute(pg.Kernel("rk4"), 6 * DAY, 1800.0)
+    ga, gr = a.get(), ref.get()
+    np.testing.assert_array_equal(ga["status"], gr["status"])
+    ok = gr["status"] == 0
+    assert np.max(cell_error(ga, gr, spec)[ok]) < 1e-5
+    assert stats["rejected"] >= 0.99 * ok.sum() * 2
+    assert stats["network_steps"] == 6 * 3000
+
+
+def test_trained_network_beats_the_24h_euler_step(env):
+    """What the trained network gains over the method without it: its 24 h
+    displacement error against RK4 is smaller than that of one 24 h Euler
+    step from the same local velocity (the network's only other source)."""
+    pg, torch, spec, fs = env
+    from paper_1707_05163_gb300 import surrogate as S
+    x, y = S.make_segments(fs, 120_000, seed=5, groups=24, period=spec.period)
+    xt, yt = S.make_segments(fs, 10_000, seed=6, groups=8, period=spec.period)
+    net = pg.MLP(37, 128, 3, 3, seed=1)
+    losses = S.train(net, x, y, steps=600, batch=4096, lr=2e-3)
+    assert losses[-1] < 0.2 * losses[0]
+    pred = net.forward(xt).cpu().numpy()
+    yt_ = yt.cpu().numpy()
+    e_net = np.mean(np.abs(pred[:, :2] - yt_[:, :2]))
+    # Euler over 24 h from the velocity interpolated at the particle (from the
+    # stencil's central cell corners), in cells of the 2-degree grid
+    f = xt.cpu().numpy()
+    xi, eta = f[:, 0], f[:, 1]
+    st = f[:, 5:].reshape(-1, 4, 4, 2)
+    u = ((1 - xi) * (1 - eta) * st[:, 1, 1, 0] + xi * (1 - eta) * st[:, 1, 2, 0] +
+         (1 - xi) * eta * st[:, 2, 1, 0] + xi * eta * st[:, 2, 2, 0]) * 0.3
+    v = ((1 - xi) * (1 - eta) * st[:, 1, 1, 1] + xi * (1 - eta) * st[:, 1, 2, 1] +
+         (1 - xi) * eta * st[:, 2, 1, 1] + xi * eta * st[:, 2, 2, 1]) * 0.3
+    D = 1852.0 * 60.0
+    lat = f[:, 2] * 90.0
+    eu = np.stack([u * DAY / (D * np.cos(np.deg2rad(lat))) / 2.0, v * DAY / D / 2.0], axis=1)
+    e_euler = np.mean(np.abs(eu - yt_[:, :2]))
+    assert e_net < e_euler, (e_net, e_euler)
