@@ -1000,7 +1000,7 @@ pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
   CU(cudaMemsetAsync(ps->d_counter, 0, 8, st));
   CU(cudaMemsetAsync(ps->d_err, 0, 4, st));
 
-  const double chunk_len = std::fabs(dt) * ps->tune.chunk_steps;
+  const double chunk_len = std::fabs(dt) * (ps->tune.chunk_steps > 0 ? ps->tune.chunk_steps : 64);
   const double resort_len = ps->tune.resort_steps > 0 ? std::fabs(dt) * ps->tune.resort_steps : 0.0;
   double next_out = output_dt > 0.0 ? t_begin + sgn * output_dt : t_end;
   double next_sort = resort_len > 0.0 ? t_begin + sgn * resort_len : t_end;
@@ -1015,6 +1015,10 @@ pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
     clip(t_end);
     clip(next_out);
     clip(next_sort);
+    if (!(sgn * (tn - tc) > 0.0)) {
+      set_error("time loop cannot advance from t = %g with dt = %g", tc, dt);
+      return PG_ERR_ARG;
+    }
     std::vector<int> need;
     if (fs->streaming && fs->nt == 1) {
       need.push_back(0);
@@ -1079,7 +1083,10 @@ pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
       if (r) return r;
     }
     if (tc == next_out) next_out = tc + sgn * output_dt;
-    if (++guard > 100000000) break;
+    if (++guard > 100000000) {
+      set_error("time loop made no progress");
+      return PG_ERR_STATE;
+    }
   }
   unsigned long long done = 0;
   int err = 0;
