@@ -52,12 +52,16 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="3d", choices=["3d", "precision", "batch"],
+    ap.add_argument("--workload", default="3d", choices=["3d", "precision", "batch", "surrogate"],
                     help="3d: the FP32 3-D workload (default); precision: 2-D 1/12 deg "
                          "cell-index + FP16/BF16 form against plain FP32; batch: 256 "
                          "releases in one persistent launch per day, graph-captured")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="shrink every release of the batch workload (tests)")
+    ap.add_argument("--train-segments", type=int, default=20_000_000)
+    ap.add_argument("--train-steps", type=int, default=20000)
+    ap.add_argument("--sur-days", type=float, default=180.0)
+    ap.add_argument("--tcgen05", action="store_true", help="surrogate GEMMs on tcgen05")
     ap.add_argument("--storage", default="f16", choices=["f16", "bf16"])
     return ap.parse_args()
 
@@ -201,6 +205,8 @@ def main():
         return precision_workload(args, rank, world, local)
     if args.workload == "batch":
         return batch_workload(args, rank, world, local)
+    if args.workload == "surrogate":
+        return surrogate_workload(args, rank, world, local)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -405,6 +411,96 @@ def reference_arm(args, rank, world):
         "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def surrogate_workload(args, rank, world, local):
+    """Learned-surrogate form: an MLP (37 inputs incl. a 4x4x2 U/V stencil, 4
+    hidden layers of 256, GELU, BF16 weights, FP32 accumulation) trained with
+    the library's kernels on RK4 24 h segments generated on the GPU over the
+    3-D 1/4-degree field (30-day periodic), then run for 10M particles over
+    180 days with an RK4 check every 5 network steps and RK4 fallback above
+    the threshold.  Compared with plain FP32 RK4 on the same particles."""
+    import torch
+    import paper_1707_05163_gb300 as pg
+    from paper_1707_05163_gb300 import surrogate as S
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gf = synth.GlobalField(res_deg=0.25, nz=50, nt=30, seed=2)
+    fs = build_fieldset_device(pg, gf, torch, dev, make_field_host_bases(gf))
+    t0 = time.perf_counter()
+    x, y = S.make_segments(fs, args.train_segments, seed=5, groups=60, period=gf.period)
+    t_data = time.perf_counter() - t0
+    xv, yv = S.make_segments(fs, 1_000_000, seed=6, groups=20, period=gf.period)
+    net = pg.MLP(37, 256, 4, 3, seed=5)
+    if args.tcgen05:
+        net.set_engine(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = S.train(net, x, y, steps=args.train_steps, batch=16384, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del x, y
+    pred = net.forward(xv)
+    err = (pred[:, :2] - yv[:, :2]).abs().max(dim=1).values.cpu().numpy()
+    held = {"mean_cells": float(err.mean()), "median_cells": float(np.median(err)),
+            "within_1e-3": float((err <= 1e-3).mean()), "within_1e-2": float((err <= 1e-2).mean()),
+            "within_1e-1": float((err <= 1e-1).mean())}
+    n = args.particles
+    nsteps = int(round(args.sur_days))
+    lon, lat, dep = synth.uniform_particles(n, 7, (0.0, 360.0), (-80.0, 80.0), (5.0, 1000.0),
+                                            dtype=np.float32)
+    dl, da, dd = (torch.from_numpy(a).to(dev) for a in (lon, lat, dep))
+    K = pg.Kernel("rk4")
+    # plain FP32 RK4 over the same horizon
+    ref = pg.ParticleSet(fs, dl, da, dd, pos="f32")
+    ref.set_tune(args.block, args.resort_steps, 48)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rk_steps = ref.execute(K, nsteps * DAY, 1800.0)
+    torch.cuda.synchronize()
+    t_rk = time.perf_counter() - t0
+    g_ref = ref.get()
+    ref.destroy()
+    runs = {}
+    for thr in (1e-3, 1e-2, 1e-1):
+        ps = pg.ParticleSet(fs, dl, da, dd, pos="f32")
+        ps.set_tune(args.block, 0, 48)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = pg.surrogate_run(ps, net, K, nsteps=nsteps, check_every=5, threshold=thr)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        g = ps.get()
+        ok = (g["status"] == 0) & (g_ref["status"] == 0)
+        dlon = (g["lon"] - g_ref["lon"] + 180.0) % 360.0 - 180.0
+        e = np.maximum(np.abs(dlon), np.abs(g["lat"] - g_ref["lat"]))[ok] / 0.25
+        runs[f"{thr:g}"] = {"seconds": dt, "speedup_vs_plain_rk4": t_rk / dt,
+                            "equivalent_rate": rk_steps / dt,
+                            "rejected_fraction": st["rejected"] / max(1, n * (nsteps // 5)),
+                            "mean_check_error_cells": st["error_sum"] / max(1, st["checked"]),
+                            "final_mean_error_vs_rk4_cells": float(e.mean()) if e.size else None,
+                            "network_seconds": st["seconds_network"],
+                            "rk4_seconds": st["seconds_rk4"]}
+        ps.destroy()
+    main = runs["0.001"]
+    line = {
+        "metric": METRIC, "value": main["equivalent_rate"], "unit": UNIT, "n_gpus": 1,
+        "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 MLP (fp32 accumulate) + f32 RK4 judge",
+        "data": "synthetic (seeded k^-3 random streamfunction field, uniform particles)",
+        "config": {"workload": f"surrogate: MLP 37-256x4-3 trained on {args.train_segments} RK4 "
+                               f"24 h segments, {n} particles x {nsteps} days, RK4 check every 5 "
+                               "steps, fallback above 1e-3 cell, 3-D 1/4 deg field",
+                   "engine": "tcgen05" if args.tcgen05 else "mma.sync",
+                   "value": "equivalent RK4 particle-steps/s (48 steps of 30 min per day)"},
+        "plain_fp32_rk4_rate": rk_steps / t_rk,
+        "speedup_vs_plain_fp32": main["speedup_vs_plain_rk4"],
+        "thresholds": runs, "held_out_24h_error": held,
+        "training": {"segments_seconds": t_data, "train_seconds": t_train,
+                     "steps": args.train_steps, "first_loss": losses[0], "last_loss": losses[-1]},
+    }
+    print(json.dumps(line), flush=True)
 
 
 def batch_workload(args, rank, world, local):

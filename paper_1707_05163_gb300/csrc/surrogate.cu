@@ -152,22 +152,25 @@ __global__ void displacement_kernel(GridArgs g, const float *lon0, const float *
 }
 
 // Position error (in cells; depth in units of the local layer) between the
-// network's state and RK4's; rejects particles above the threshold or whose
-// status differs.  err_sum[0] += error over particles both keep alive,
-// err_sum[1] += count.
+// network's state and RK4's; rejects particles above the threshold, and any
+// particle alive at the block's start that the network or the judge deleted
+// within the block (RK4 from the block's start then decides).  err_sum[0] +=
+// error over particles both keep alive, err_sum[1] += count.
 __global__ void check_kernel(GridArgs g, const float *lon_a, const float *lat_a,
                              const float *dep_a, const uint8_t *st_a, const float *lon_b,
                              const float *lat_b, const float *dep_b, const uint8_t *st_b,
-                             int64_t n, float threshold, uint8_t *reject, double *err_sum,
-                             unsigned long long *n_reject) {
+                             const uint8_t *st_ckpt, int64_t n, float threshold, uint8_t *reject,
+                             double *err_sum, unsigned long long *n_reject) {
   double e_acc = 0.0, c_acc = 0.0;
   unsigned long long r_acc = 0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     uint8_t rj = 0;
-    if (st_a[p] != st_b[p]) {
-      rj = 1;
-    } else if (st_b[p] == 0) {
+    if (st_ckpt[p] != 0) {
+      rj = 0;              // deleted before the block: stays deleted
+    } else if (st_a[p] != 0 || st_b[p] != 0) {
+      rj = 1;              // a deletion inside the block is decided by RK4 alone
+    } else {
       float dl = lon_a[p] - lon_b[p];
       if (g.periodic) {
         if (dl > 180.f) dl -= 360.f;
@@ -425,7 +428,7 @@ pg_status pg_surrogate_run(pg_pset *ps, pg_mlp *net, const pg_kernel *k, int nst
     check_kernel<<<grid_of(n, sm), 256, 0, st>>>(
         grid_args_of(ps->fs), (const float *)ps->x, (const float *)ps->y, (const float *)ps->z,
         ps->status, (const float *)chk->x, (const float *)chk->y, (const float *)chk->z,
-        chk->status, n, (float)threshold, rej, esum, nrej);
+        chk->status, ckpt->status, n, (float)threshold, rej, esum, nrej);
     note_launches(1);
     double h_esum[2];
     unsigned long long h_nrej = 0;
