@@ -339,6 +339,7 @@ struct pg_mlp {
   __nv_bfloat16 *dyb = nullptr, *dyt = nullptr, *xt = nullptr;   // BF16 grads, transposes
   float *loss_partial = nullptr;
   int use_tc = 0;                     // tcgen05 forward when available
+  int *d_err = nullptr;               // device word: tcgen05 wait gave up
 };
 
 namespace pg {
@@ -417,11 +418,12 @@ cudaError_t forward(pg_mlp *n, int64_t rows, cudaStream_t st, bool keep) {
     const __nv_bfloat16 *W = n->wb + n->woff[l];
     const float *b = n->w + n->boff[l];
     cudaError_t e;
-    if (n->use_tc) {
-      int err = 0;
+    const bool tc_shape = (n->dout[l] == 64 || n->dout[l] == 256) &&
+                          (n->din[l] == 64 || n->din[l] == 256);
+    if (n->use_tc && tc_shape) {
       e = gemm_nt_tc(x, ldx, W, n->din[l], rows, n->dout[l], n->din[l], b, last ? 0 : 1,
                      last ? n->y : nullptr, last ? nullptr : n->act[l],
-                     (!last && keep) ? n->pre[l] : nullptr, n->dout[l], st, &err);
+                     (!last && keep) ? n->pre[l] : nullptr, n->dout[l], st, n->d_err);
     } else {
       e = gemm_nt(x, ldx, W, n->din[l], rows, n->dout[l], n->din[l], b, last ? 0 : 1,
                   last ? n->y : nullptr, last ? nullptr : n->act[l],
@@ -528,6 +530,8 @@ pg_status pg_mlp_create(int n_in, int width, int depth, int n_out, uint64_t seed
   if (e == cudaSuccess) e = dev_alloc((void **)&n->g, off * 4);
   if (e == cudaSuccess) e = dev_alloc((void **)&n->wb, off * 2);
   if (e == cudaSuccess) e = dev_alloc((void **)&n->wbt, off * 2);
+  if (e == cudaSuccess) e = dev_alloc((void **)&n->d_err, 4);
+  if (e == cudaSuccess) e = cudaMemset(n->d_err, 0, 4);
   if (e == cudaSuccess) e = cudaMemcpy(n->w, h.data(), off * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(n->m, 0, off * 4);
   if (e == cudaSuccess) e = cudaMemset(n->v, 0, off * 4);
@@ -537,6 +541,7 @@ pg_status pg_mlp_create(int n_in, int width, int depth, int n_out, uint64_t seed
   if (e != cudaSuccess) {
     dev_free(n->w); dev_free(n->m); dev_free(n->v); dev_free(n->g); dev_free(n->wb);
     dev_free(n->wbt);
+    dev_free(n->d_err);
     delete n;
     cudaGetLastError();
     set_error("MLP allocation failed: %s", cudaGetErrorString(e));
@@ -552,6 +557,7 @@ pg_status pg_mlp_destroy(pg_mlp *n) {
   free_ws(n);
   dev_free(n->w); dev_free(n->m); dev_free(n->v); dev_free(n->g); dev_free(n->wb);
   dev_free(n->wbt);
+  dev_free(n->d_err);
   delete n;
   return PG_OK;
 }
@@ -612,6 +618,15 @@ pg_status pg_mlp_forward(pg_mlp *n, const float *x, int64_t M, float *y, void *s
                           cudaMemcpyDeviceToDevice, st));
   }
   CUM(cudaGetLastError());
+  if (n->use_tc) {
+    int err = 0;
+    CUM(cudaMemcpyAsync(&err, n->d_err, 4, cudaMemcpyDeviceToHost, st));
+    CUM(cudaStreamSynchronize(st));
+    if (err) {
+      set_error("tcgen05 product gave up waiting for its accumulator");
+      return PG_ERR_TIMEOUT;
+    }
+  }
   return PG_OK;
 }
 

@@ -1,13 +1,230 @@
-// mlp_tc.cu -- forward GEMM on the 5th-generation tensor cores (tcgen05).
+// mlp_tc.cu -- the MLP's forward products on the 5th-generation tensor cores.
+//
+// out[M x N] = act(A[M x K] . B[N x K]^T + bias), BF16 operands, FP32
+// accumulation in tensor memory (TMEM), N and K in {64, 256}.  Persistent
+// CTAs (one per SM): each loads B once into shared memory and then walks
+// 128-row tiles of A.  Per tile: the 128 threads copy the A tile into shared
+// memory, one thread issues K/16 tcgen05.mma (128 x N x 16) and commits them
+// to an mbarrier, all threads wait on it (bounded), then each warp reads its
+// 32 accumulator rows from TMEM (tcgen05.ld) and applies bias, GELU and the
+// BF16/FP32 stores.
+//
+// Shared-memory operand layout (K-major, no swizzle): 8-row x 16-byte core
+// matrices; core matrix (row group g, 16-byte K chunk c) sits at byte
+// (g * K/8 + c) * 128, so neighbouring K chunks are 128 bytes apart (the
+// descriptor's leading-dimension offset) and neighbouring row groups K/8 *
+// 128 bytes apart (its stride-dimension offset).
 #include <cuda_bf16.h>
 
 #include "pg_host.h"
 
 namespace pg {
 
-cudaError_t gemm_nt_tc(const __nv_bfloat16 *, int, const __nv_bfloat16 *, int, int64_t, int, int,
-                       const float *, int, float *, __nv_bfloat16 *, __nv_bfloat16 *, int,
-                       cudaStream_t, int *) {
+namespace {
+
+constexpr int TM = 128;
+constexpr int kTcThreads = 128;
+constexpr long long kSpinLimit = 20000000;   // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t su32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ float gelu_tc(float x) {
+  return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
+}
+
+// 64-bit shared-memory matrix descriptor: start address, leading and stride
+// byte offsets (all >> 4), the fixed 0b001 at bits 46-48, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
+  d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major.
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+// copy rows [0, rows) of a K-wide BF16 matrix (row stride ld) into the
+// core-matrix layout; rows in [rows, R) are zero-filled
+template <int K>
+__device__ __forceinline__ void load_tile(uint8_t *dst, const __nv_bfloat16 *src, int ld, int rows,
+                                          int R) {
+  constexpr int KC = K / 8;   // 16-byte chunks per row
+  for (int idx = threadIdx.x; idx < R * KC; idx += kTcThreads) {
+    const int r = idx / KC, c = idx - r * KC;
+    const uint32_t off = (uint32_t)(((r >> 3) * KC + c) * 128 + (r & 7) * 16);
+    const bool ok = r < rows;
+    const __nv_bfloat16 *s = src + (size_t)(ok ? r : 0) * ld + c * 8;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(su32(dst + off)),
+                 "l"(s), "r"(ok ? 16 : 0));
+  }
+}
+
+template <int N, int K>
+__global__ void __launch_bounds__(kTcThreads, 1)
+gemm_tc_kernel(const __nv_bfloat16 *__restrict__ A, int lda, const __nv_bfloat16 *__restrict__ B,
+               int ldb, int64_t M, const float *__restrict__ bias, int act, float *out_f32,
+               __nv_bfloat16 *out_bf16, __nv_bfloat16 *pre_bf16, int ldc, int *err) {
+  constexpr int NCOLS = N < 32 ? 32 : N;       // TMEM columns (power of two >= 32)
+  constexpr uint32_t SB = N * K * 2, SA = TM * K * 2;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t *sB = smem;
+  uint8_t *sA = smem + SB;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + SB + SA);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + SB + SA + 8);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (M + TM - 1) / TM;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     su32(tslot)), "r"(NCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n");
+  }
+  load_tile<K>(sB, B, ldb, N, N);
+  asm volatile("cp.async.commit_group;\n");
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = instr_desc(TM, N);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    const int64_t m0 = tile * TM;
+    const int rows = (int)((M - m0) < TM ? (M - m0) : TM);
+    load_tile<K>(sA, A + (size_t)m0 * lda, lda, rows, TM);
+    asm volatile("cp.async.commit_group;\n");
+    asm volatile("cp.async.wait_group 0;\n");
+    asm volatile("fence.proxy.async.shared::cta;\n");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+#pragma unroll
+      for (int ks = 0; ks < K / 16; ++ks) {
+        const uint64_t da = smem_desc(su32(sA) + ks * 256, 128, (K / 8) * 128);
+        const uint64_t db = smem_desc(su32(sB) + ks * 256, 128, (K / 8) * 128);
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(ks));
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              su32(mbar)));
+    }
+    // wait for the accumulator (bounded)
+    {
+      uint32_t done = 0;
+      long long spins = 0;
+      while (!done) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(su32(mbar)), "r"(phase));
+        if (!done && ++spins > kSpinLimit) break;
+      }
+      if (!done) {
+        if (threadIdx.x == 0) atomicCAS(err, 0, 1);
+        failed = true;
+      }
+    }
+    phase ^= 1u;
+    if (failed) break;
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const int64_t row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+          "%14,%15}, [%16];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+            "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+      if (row < M) {
+        const size_t o = (size_t)row * ldc + c0;
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
+          if (bias) { v0 += bias[c0 + j]; v1 += bias[c0 + j + 1]; }
+          if (pre_bf16)
+            *reinterpret_cast<__nv_bfloat162 *>(pre_bf16 + o + j) = __floats2bfloat162_rn(v0, v1);
+          if (act == 1) { v0 = gelu_tc(v0); v1 = gelu_tc(v1); }
+          if (out_f32) { out_f32[o + j] = v0; out_f32[o + j + 1] = v1; }
+          if (out_bf16)
+            *reinterpret_cast<__nv_bfloat162 *>(out_bf16 + o + j) = __floats2bfloat162_rn(v0, v1);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(NCOLS));
+  }
+}
+
+template <int N, int K>
+cudaError_t launch_tc(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int64_t M,
+                      const float *bias, int act, float *out_f32, __nv_bfloat16 *out_bf16,
+                      __nv_bfloat16 *pre_bf16, int ldc, cudaStream_t st, int *err) {
+  constexpr size_t smem = (size_t)N * K * 2 + (size_t)TM * K * 2 + 16;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<N, K>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t ntiles = (M + TM - 1) / TM;
+  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  gemm_tc_kernel<N, K><<<grid, kTcThreads, smem, st>>>(A, lda, B, ldb, M, bias, act, out_f32,
+                                                       out_bf16, pre_bf16, ldc, err);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Forward products of the MLP on tcgen05; N and K must be 64 or 256, all row
+// strides multiples of 8 elements.  *err (device) is set to 1 if a CTA gave
+// up waiting for its accumulator.
+cudaError_t gemm_nt_tc(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
+                       int64_t M, int N, int K, const float *bias, int act, float *out_f32,
+                       __nv_bfloat16 *out_bf16, __nv_bfloat16 *pre_bf16, int ldc, cudaStream_t st,
+                       int *err) {
+  if (M == 0) return cudaSuccess;
+  if (lda % 8 || ldb % 8 || ldc % 2 || !err) return cudaErrorInvalidValue;
+  if (N == 256 && K == 256)
+    return launch_tc<256, 256>(A, lda, B, ldb, M, bias, act, out_f32, out_bf16, pre_bf16, ldc, st, err);
+  if (N == 256 && K == 64)
+    return launch_tc<256, 64>(A, lda, B, ldb, M, bias, act, out_f32, out_bf16, pre_bf16, ldc, st, err);
+  if (N == 64 && K == 256)
+    return launch_tc<64, 256>(A, lda, B, ldb, M, bias, act, out_f32, out_bf16, pre_bf16, ldc, st, err);
+  if (N == 64 && K == 64)
+    return launch_tc<64, 64>(A, lda, B, ldb, M, bias, act, out_f32, out_bf16, pre_bf16, ldc, st, err);
   return cudaErrorNotSupported;
 }
 

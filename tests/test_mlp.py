@@ -129,3 +129,22 @@ def test_training_reduces_loss_on_a_smooth_map(gpu):
     for _ in range(400):
         last = net.train_step(xd, td, 2e-3)
     assert last < 0.05 * first, (first, last)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("M", [1, 127, 128, 129, 5000, 262151])
+def test_tcgen05_forward_matches_mma_sync(gpu, M):
+    """The tcgen05 engine (TMEM accumulators) and the mma.sync engine multiply
+    the same BF16 operands with FP32 accumulation; they differ only in the
+    order of the additions and in the BF16 rounding that follows."""
+    pg, torch = gpu
+    net = pg.MLP(37, 256, 4, 3, seed=11)
+    rng = np.random.default_rng(M)
+    x = torch.from_numpy(rng.normal(size=(M, 37)).astype(np.float32)).cuda()
+    net.set_engine(False)
+    y0 = net.forward(x).cpu().numpy()
+    net.set_engine(True)
+    y1 = net.forward(x).cpu().numpy()
+    y2 = net.forward(x).cpu().numpy()
+    np.testing.assert_array_equal(y1, y2)
+    _close(y1, y0, rel=1e-2)
