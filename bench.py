@@ -441,6 +441,23 @@ def surrogate_workload(args, rank, world, local):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del x, y
+    # forward throughput of the two tensor-core engines on 10M feature rows
+    # (padded network: 2 * (64*256 + 3*256*256 + 256*64) FLOP per row)
+    flop_row = 2.0 * (64 * 256 + 3 * 256 * 256 + 256 * 64)
+    xb = xv.repeat((10_000_000 + xv.shape[0] - 1) // xv.shape[0], 1)[:10_000_000].contiguous()
+    engines = {}
+    for name, flag in (("mma.sync", False), ("tcgen05", True)):
+        net.set_engine(flag)
+        net.forward(xb)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            net.forward(xb)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) / 3 * 1e3
+        engines[name] = {"ms_per_10M_rows": ms, "TFLOPs": flop_row * 1e7 / (ms * 1e-3) / 1e12}
+    del xb
+    net.set_engine(bool(args.tcgen05))
     pred = net.forward(xv)
     err = (pred[:, :2] - yv[:, :2]).abs().max(dim=1).values.cpu().numpy()
     held = {"mean_cells": float(err.mean()), "median_cells": float(np.median(err)),
@@ -496,7 +513,7 @@ def surrogate_workload(args, rank, world, local):
                    "value": "equivalent RK4 particle-steps/s (48 steps of 30 min per day)"},
         "plain_fp32_rk4_rate": rk_steps / t_rk,
         "speedup_vs_plain_fp32": main["speedup_vs_plain_rk4"],
-        "thresholds": runs, "held_out_24h_error": held,
+        "thresholds": runs, "held_out_24h_error": held, "mlp_forward": engines,
         "training": {"segments_seconds": t_data, "train_seconds": t_train,
                      "steps": args.train_steps, "first_loss": losses[0], "last_loss": losses[-1]},
     }

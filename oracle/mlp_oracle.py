@@ -1,7 +1,8 @@
 """FP64 CPU oracle of the surrogate MLP (test infrastructure only).
 
 Network: x -> (W_l x + b_l, GELU) for the hidden layers -> W_L x + b_L, with
-GELU(x) = x/2 (1 + erf(x / sqrt 2)); loss L = 0.5 mean_rows sum_out (y - t)^2.
+GELU in its tanh form x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))); loss
+L = 0.5 mean_rows sum_out (y - t)^2.
 Parameters use the padded layout of the CUDA library (per layer W [dout x
 din] row-major, then b [dout]); the oracle reads only the real block.  The
 backward pass is written out by the chain rule; the tests pin it to central
@@ -12,17 +13,19 @@ from __future__ import annotations
 import math
 
 import numpy as np
-from scipy.special import erf
+
+
+_C = math.sqrt(2.0 / math.pi)
 
 
 def _gelu(x):
-    return 0.5 * x * (1.0 + erf(x / math.sqrt(2.0)))
+    """GELU in its tanh form: x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))."""
+    return 0.5 * x * (1.0 + np.tanh(_C * (x + 0.044715 * x ** 3)))
 
 
 def _gelu_grad(x):
-    cdf = 0.5 * (1.0 + erf(x / math.sqrt(2.0)))
-    pdf = np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
-    return cdf + x * pdf
+    t = np.tanh(_C * (x + 0.044715 * x ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * _C * (1.0 + 3 * 0.044715 * x * x)
 
 
 def pad64(n):

@@ -30,8 +30,12 @@ __device__ __forceinline__ uint32_t su32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// GELU in its tanh form (as in mlp.cu), hardware tanh approximation.
 __device__ __forceinline__ float gelu_tc(float x) {
-  return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
+  const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+  return 0.5f * x * (1.0f + t);
 }
 
 // 64-bit shared-memory matrix descriptor: start address, leading and stride
