@@ -49,8 +49,6 @@ def parse():
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--resort-steps", type=int, default=96)
     ap.add_argument("--chunk-steps", type=int, default=48)
-    ap.add_argument("--cache", type=int, default=0, choices=[0, 1],
-                    help="cell corner values in registers (0) or shared memory (1)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -244,7 +242,7 @@ def main():
 
     def one_step(timing=False):
         ps = pg.ParticleSet(fs, dlon, dlat, ddep, pos="f32", seed=0)
-        ps.set_tune(args.block, args.resort_steps, args.chunk_steps, args.cache)
+        ps.set_tune(args.block, args.resort_steps, args.chunk_steps)
         if timing:
             lib.pg_pset_kernel_timing(ps.h, 1, None, None)
         steps = ps.execute(kern, runtime, 1800.0)
@@ -365,7 +363,7 @@ def e2e_leg(pg, gf, torch, host_field, lon, lat, dep, kern, runtime, args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ps = pg.ParticleSet(fs, hl, ha, hd, pos="f32", seed=0)
-        ps.set_tune(args.block, args.resort_steps, args.chunk_steps, args.cache)
+        ps.set_tune(args.block, args.resort_steps, args.chunk_steps)
         steps = ps.execute(kern, runtime, 1800.0)
         ps.get_into(lon=out["lon"], lat=out["lat"], depth=out["depth"], status=ost)
         torch.cuda.synchronize()

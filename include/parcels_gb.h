@@ -114,8 +114,6 @@ typedef struct {
     int block;          /* threads per block of the advection kernel (default 256)  */
     int resort_steps;   /* Morton re-sort every this many steps (0: never)           */
     int chunk_steps;    /* at most this many steps per kernel launch (default 64)    */
-    int cache;          /* FP32 kernels: cell corner values in registers (0) or in
-                           shared memory (1), which leaves more room for warps     */
 } pg_tune;
 
 /* Snapshot source for streamed fields (the counterpart of advancing the

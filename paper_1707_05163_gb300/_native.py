@@ -41,8 +41,7 @@ class Grid(C.Structure):
 
 
 class Tune(C.Structure):
-    _fields_ = [("block", C.c_int), ("resort_steps", C.c_int), ("chunk_steps", C.c_int),
-                ("cache", C.c_int)]
+    _fields_ = [("block", C.c_int), ("resort_steps", C.c_int), ("chunk_steps", C.c_int)]
 
 
 class SurrogateStats(C.Structure):

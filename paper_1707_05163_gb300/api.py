@@ -234,8 +234,8 @@ class ParticleSet:
         N.check(self._lib.pg_pset_size(self.h, C.byref(n), C.byref(a)))
         return a.value
 
-    def set_tune(self, block=0, resort_steps=0, chunk_steps=0, cache=0):
-        t = N.Tune(int(block), int(resort_steps), int(chunk_steps), int(cache))
+    def set_tune(self, block=0, resort_steps=0, chunk_steps=0):
+        t = N.Tune(int(block), int(resort_steps), int(chunk_steps))
         N.check(self._lib.pg_pset_set_tune(self.h, C.byref(t)))
 
     def execute(self, kernel: Kernel, runtime, dt, output_dt=0.0,
@@ -332,8 +332,7 @@ def execute_batch(psets, kernels, runtimes, dts, window=86400.0, tune=None, tune
     k_arr = (C.c_void_p * nrel)(*[k.h.value for k in kernels])
     rt = np.ascontiguousarray(runtimes, dtype=np.float64)
     dt = np.ascontiguousarray(dts, dtype=np.float64)
-    t_in = N.Tune(int(tune[0]), int(tune[1]), 0, int(tune[2]) if len(tune) > 2 else 0) \
-        if tune is not None else None
+    t_in = N.Tune(int(tune[0]), int(tune[1]), 0) if tune is not None else None
     chosen = N.Tune()
     steps = C.c_int64()
     N.check(lib.pg_execute_batch(nrel, ps_arr, k_arr, rt.ctypes.data, dt.ctypes.data,
@@ -341,7 +340,7 @@ def execute_batch(psets, kernels, runtimes, dts, window=86400.0, tune=None, tune
                                  C.byref(chosen),
                                  str(tune_cache).encode() if tune_cache else None,
                                  int(bool(use_graph)), _stream(stream), C.byref(steps)))
-    return steps.value, (chosen.block, chosen.resort_steps, chosen.cache)
+    return steps.value, (chosen.block, chosen.resort_steps)
 
 
 class MLP:

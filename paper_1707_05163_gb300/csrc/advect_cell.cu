@@ -6,31 +6,20 @@
 
 namespace pg {
 
-template <typename Store, bool SM>
+template <typename Store>
 static cudaError_t launch_cell(const StepArgs &a, int block, cudaStream_t st) {
   if (a.p.n == 0) return cudaSuccess;
   const bool d3 = a.g.nz > 1;
-  if (a.f.nf == 3)
-    return launch_clamped(advect_cell_kernel<Store, 3, true, SM>, a, block, st,
-                          SM ? corner_smem_bytes(3, true, 1) : 0);
-  if (d3)
-    return launch_clamped(advect_cell_kernel<Store, 2, true, SM>, a, block, st,
-                          SM ? corner_smem_bytes(2, true, 1) : 0);
-  return launch_clamped(advect_cell_kernel<Store, 2, false, SM>, a, block, st,
-                        SM ? corner_smem_bytes(2, false, 1) : 0);
+  if (a.f.nf == 3) return launch_clamped(advect_cell_kernel<Store, 3, true>, a, block, st);
+  if (d3) return launch_clamped(advect_cell_kernel<Store, 2, true>, a, block, st);
+  return launch_clamped(advect_cell_kernel<Store, 2, false>, a, block, st);
 }
 
-template <typename Store>
-static cudaError_t launch_cell_any(const StepArgs &a, int block, cudaStream_t st, int cache) {
-  return cache ? launch_cell<Store, true>(a, block, st) : launch_cell<Store, false>(a, block, st);
-}
-
-cudaError_t launch_advect_cell(const StepArgs &a, int storage, int block, cudaStream_t st,
-                               int cache) {
+cudaError_t launch_advect_cell(const StepArgs &a, int storage, int block, cudaStream_t st) {
   switch (storage) {
-    case PG_F32: return launch_cell_any<float>(a, block, st, cache);
-    case PG_F16S: return launch_cell_any<__half>(a, block, st, cache);
-    case PG_BF16S: return launch_cell_any<__nv_bfloat16>(a, block, st, cache);
+    case PG_F32: return launch_cell<float>(a, block, st);
+    case PG_F16S: return launch_cell<__half>(a, block, st);
+    case PG_BF16S: return launch_cell<__nv_bfloat16>(a, block, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -42,8 +42,8 @@ __device__ __forceinline__ bool norm_axis(int &i, float &f, int n, bool periodic
 }
 
 // Velocity in cells per second at the stage position base + kc * off.
-template <typename Store, int NF, bool D3, bool SM>
-__device__ __forceinline__ int velocity_cell(const StepArgs &a, Sampler<float, Store, NF, D3, SM> &c,
+template <typename Store, int NF, bool D3>
+__device__ __forceinline__ int velocity_cell(const StepArgs &a, Sampler<float, Store, NF, D3> &c,
                                              Clock &ck, float off, const CellState &b,
                                              const float (&kc)[3], float (&vel)[3]) {
   const GridArgs &g = a.g;
@@ -72,8 +72,8 @@ __device__ __forceinline__ int velocity_cell(const StepArgs &a, Sampler<float, S
 }
 
 // One step of Eq. 1 in cell units; the state is replaced only on success.
-template <typename Store, int NF, bool D3, bool SM>
-__device__ __forceinline__ int step_cell(const StepArgs &a, Sampler<float, Store, NF, D3, SM> &c,
+template <typename Store, int NF, bool D3>
+__device__ __forceinline__ int step_cell(const StepArgs &a, Sampler<float, Store, NF, D3> &c,
                                          Clock &ck, CellState &s, float h, uint64_t id,
                                          uint32_t stp) {
   const GridArgs &g = a.g;
@@ -118,8 +118,8 @@ __device__ __forceinline__ int step_cell(const StepArgs &a, Sampler<float, Store
   return 0;
 }
 
-template <typename Store, int NF, bool D3, bool SM>
-__global__ void __launch_bounds__(256, SM ? 3 : 2) advect_cell_kernel(StepArgs a) {
+template <typename Store, int NF, bool D3>
+__global__ void __launch_bounds__(256, 2) advect_cell_kernel(StepArgs a) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long done = 0;
   if (p < a.p.n && a.p.status[p] == 0) {
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256, SM ? 3 : 2) advect_cell_kernel(StepArgs a
     uint32_t stp = a.p.step[p];
     const uint64_t id = a.p.id[p];
     uint8_t st = 0;
-    Sampler<float, Store, NF, D3, SM> c;
+    Sampler<float, Store, NF, D3> c;
     c.reset();
     const double sgn = a.dt > 0.0 ? 1.0 : -1.0;
     // the step count of this chunk is fixed up front; step k starts at

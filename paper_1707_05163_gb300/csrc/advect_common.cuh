@@ -127,41 +127,7 @@ __device__ __forceinline__ int axis_search(const GridArgs &g, int a, int n, Real
 }
 
 // ---------------------------------------------------------- the sampler ---
-// Corner values of the cached cell for the two snapshots: in registers
-// (SM = false) or in a [value][thread] column of dynamic shared memory
-// (SM = true; conflict-free, frees 48 registers in 3-D for more resident
-// warps).
-extern __shared__ float pg_corner_smem[];
-
-template <typename Real, int NF, int NC, bool SM> struct Corners;
-template <typename Real, int NF, int NC> struct Corners<Real, NF, NC, false> {
-  Real v[2][NF][NC];
-  __device__ __forceinline__ void init() {}
-  __device__ __forceinline__ Real get(int sl, int f, int q) const { return v[sl][f][q]; }
-  __device__ __forceinline__ void set(int sl, int f, int q, Real x) { v[sl][f][q] = x; }
-};
-template <typename Real, int NF, int NC> struct Corners<Real, NF, NC, true> {
-  static_assert(sizeof(Real) == 4, "shared-memory corners hold FP32 values");
-  float *base;
-  int stride;
-  __device__ __forceinline__ void init() {
-    base = pg_corner_smem + threadIdx.x;
-    stride = blockDim.x;
-  }
-  __device__ __forceinline__ Real get(int sl, int f, int q) const {
-    return base[((sl * NF + f) * NC + q) * stride];
-  }
-  __device__ __forceinline__ void set(int sl, int f, int q, Real x) {
-    base[((sl * NF + f) * NC + q) * stride] = x;
-  }
-};
-
-// Dynamic shared memory the SM = true kernels need per block.
-__host__ __device__ constexpr size_t corner_smem_bytes(int nf, bool d3, int block) {
-  return (size_t)2 * nf * (d3 ? 8 : 4) * 4 * block;
-}
-
-template <typename Real, typename Store, int NF, bool D3, bool SM = false>
+template <typename Real, typename Store, int NF, bool D3>
 struct Sampler {
   static constexpr int NC = D3 ? 8 : 4;
   // cached cell (ci = -1: none) and its bounds
@@ -173,11 +139,10 @@ struct Sampler {
   int gi, gj, gk, gs0, gs1;   // what `v` currently holds (gi = -1: nothing)
   double ta;                  // FP32 path: interval start in unwrapped time
   float span, rspan;          // FP32 path
-  Corners<Real, NF, NC, SM> v;
+  Real v[2][NF][NC];
 
   __device__ __forceinline__ void reset() {
     ci = -1; cj = -1; ck = -1; s0 = -1; s1 = -1; gi = -1;
-    v.init();
   }
 };
 
@@ -245,8 +210,8 @@ __device__ __forceinline__ bool time_interval(const FieldArgs &f, double t, int 
   return true;
 }
 
-template <typename Real, typename Store, int NF, bool D3, bool SM>
-__device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Store, NF, D3, SM> &c,
+template <typename Real, typename Store, int NF, bool D3>
+__device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
                                             int sl, int s) {
   const GridArgs &g = a.g;
   const Store *base = reinterpret_cast<const Store *>(a.f.tab[s]);
@@ -269,7 +234,7 @@ __device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Sto
         Real vv[NF];
         load_node<Real, NF>(base, row + (size_t)(ii ? c.ci1 : c.ci), sc, vv);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) c.v.set(sl, f, kk * 4 + jj * 2 + ii, vv[f]);
+        for (int f = 0; f < NF; ++f) c.v[sl][f][kk * 4 + jj * 2 + ii] = vv[f];
       }
     }
   }
@@ -279,8 +244,8 @@ __device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Sto
 // Make `v` hold the corners of the cached cell for snapshots s0 and s1.  If
 // only the snapshot pair moved on by one, the shared snapshot's corners move
 // from slot 1 to slot 0 and only the new snapshot is read.
-template <typename Real, typename Store, int NF, bool D3, bool SM>
-__device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, NF, D3, SM> &c,
+template <typename Real, typename Store, int NF, bool D3>
+__device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
                                        bool steady) {
   const bool same_cell = c.gi == c.ci && c.gj == c.cj && c.gk == c.ck && c.gi >= 0;
   if (steady) {
@@ -289,7 +254,7 @@ __device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, N
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
-      for (int q = 0; q < Sampler<Real, Store, NF, D3, SM>::NC; ++q) c.v.set(0, f, q, c.v.get(1, f, q));
+      for (int q = 0; q < Sampler<Real, Store, NF, D3>::NC; ++q) c.v[0][f][q] = c.v[1][f][q];
     if (!gather_slab(a, c, 1, c.s1)) return false;
   } else {
     if (!gather_slab(a, c, 0, c.s0)) return false;
@@ -352,8 +317,8 @@ __device__ __forceinline__ float w_of(const KernArgs &k, float) { return k.w_sin
 // (step start + off), corner gather if the cell or interval changed, spatial
 // interpolation in each snapshot, then linear interpolation in time.
 // Returns 0, PG_NAN (3), or -1 for an internal failure recorded in a.err.
-template <typename Real, typename Store, int NF, bool D3, bool SM>
-__device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, Store, NF, D3, SM> &c,
+template <typename Real, typename Store, int NF, bool D3>
+__device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
                                              Clock &ck, Real off, Real xi, Real eta, Real zeta,
                                              Real (&vel)[3]) {
   const bool steady = a.f.nt == 1;
@@ -398,16 +363,9 @@ __device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, St
   }
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    constexpr int NC = Sampler<Real, Store, NF, D3, SM>::NC;
-    Real c0[NC];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) c0[q] = c.v.get(0, f, q);
-    Real val = interp_space<Real, NC>(c0, xi, eta, zeta);
+    Real val = interp_space<Real, Sampler<Real, Store, NF, D3>::NC>(c.v[0][f], xi, eta, zeta);
     if (!steady) {
-      Real c1[NC];
-#pragma unroll
-      for (int q = 0; q < NC; ++q) c1[q] = c.v.get(1, f, q);
-      const Real b = interp_space<Real, NC>(c1, xi, eta, zeta);
+      const Real b = interp_space<Real, Sampler<Real, Store, NF, D3>::NC>(c.v[1][f], xi, eta, zeta);
       // FP64: the definition's a + (b - a) tau.  FP32: (1 - tau) a + tau b,
       // exact at both ends, so a stage time on a snapshot gives the same
       // value from either neighbouring interval (results do not depend on

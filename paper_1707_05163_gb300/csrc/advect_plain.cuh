@@ -26,8 +26,8 @@ namespace pg {
 
 // Locate p on the longitude axis, using and refreshing the cache.
 // Returns false when the position is out of the domain.
-template <typename Real, typename Store, int NF, bool D3, bool SM>
-__device__ __forceinline__ bool locate_lon(const GridArgs &g, Sampler<Real, Store, NF, D3, SM> &c,
+template <typename Real, typename Store, int NF, bool D3>
+__device__ __forceinline__ bool locate_lon(const GridArgs &g, Sampler<Real, Store, NF, D3> &c,
                                            Real p, Real &xi) {
   Real q = p;
   const Real *x = axis<Real>(g, 0);
@@ -72,8 +72,8 @@ __device__ __forceinline__ bool locate_axis(const GridArgs &g, int a, int n, int
 // Velocity in position units per second at a stage (stage time = step start
 // + off).  Returns 0 or a particle status (PG_OOB_*, PG_NAN); -1 for an
 // internal failure already recorded in a.err.
-template <typename Real, typename Store, int NF, bool D3, bool SM>
-__device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, NF, D3, SM> &c,
+template <typename Real, typename Store, int NF, bool D3>
+__device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
                                         Clock &ck, Real off, Real lon, Real lat, Real dep,
                                         Real (&vel)[3]) {
   const GridArgs &g = a.g;
@@ -97,8 +97,8 @@ __device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, 
 // One step of Eq. 1.  Returns 0 and updates (lon, lat, dep) on success.
 // RK4 stages run in a loop: stage s samples at (X + k_{s-1} c_s h, t + c_s h)
 // with c = (0, 1/2, 1/2, 1) and accumulates ((k1 + 2 k2) + 2 k3) + k4.
-template <typename Real, typename Store, int NF, bool D3, bool SM>
-__device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, NF, D3, SM> &c,
+template <typename Real, typename Store, int NF, bool D3>
+__device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
                                         Clock &ck, Real &lon, Real &lat, Real &dep, Real hr,
                                         uint64_t id, uint32_t stp) {
   Real kc[3] = {(Real)0, (Real)0, (Real)0};
@@ -158,7 +158,7 @@ __device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, 
 // The chunk kernel: each thread advances one particle while its time is
 // before t_stop and t_end (in the direction of dt), shortening only the step
 // that lands on t_end.  Returns the number of steps taken.
-template <typename Real, typename Store, int NF, bool D3, bool SM>
+template <typename Real, typename Store, int NF, bool D3>
 __device__ __forceinline__ unsigned long long advance_particle(const StepArgs &a, int64_t p) {
   unsigned long long done = 0;
   {
@@ -170,7 +170,7 @@ __device__ __forceinline__ unsigned long long advance_particle(const StepArgs &a
     uint32_t stp = a.p.step[p];
     const uint64_t id = a.p.id[p];
     uint8_t st = 0;
-    Sampler<Real, Store, NF, D3, SM> c;
+    Sampler<Real, Store, NF, D3> c;
     c.reset();
     const double sgn = a.dt > 0.0 ? 1.0 : -1.0;
     Clock ck;
@@ -232,14 +232,11 @@ __device__ __forceinline__ void count_steps(unsigned long long done, unsigned lo
 // FP32: at most 128 registers (two 256-thread blocks per SM); measured
 // faster than the unbounded allocation despite a few spilled words, as more
 // resident warps hide the gather and dependency latencies.
-// With the corners in shared memory (SM) the cap is 80 registers (three
-// blocks of 256 threads per SM).
-template <typename Real, typename Store, int NF, bool D3, bool SM>
-__global__ void __launch_bounds__(256, SM ? 3 : (sizeof(Real) == 4 ? 2 : 1))
-    advect_plain_kernel(StepArgs a) {
+template <typename Real, typename Store, int NF, bool D3>
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1) advect_plain_kernel(StepArgs a) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long done = 0;
-  if (p < a.p.n && a.p.status[p] == 0) done = advance_particle<Real, Store, NF, D3, SM>(a, p);
+  if (p < a.p.n && a.p.status[p] == 0) done = advance_particle<Real, Store, NF, D3>(a, p);
   count_steps(done, a.steps_done);
 }
 
@@ -268,8 +265,8 @@ struct BatchArgs {
 
 // The argument block of the current tile's release is assembled once per
 // tile in shared memory, which every thread of the tile then reads.
-template <typename Store, int NF, bool D3, bool SM>
-__global__ void __launch_bounds__(256, SM ? 3 : 2) advect_batch_kernel(BatchArgs b) {
+template <typename Store, int NF, bool D3>
+__global__ void __launch_bounds__(256, 2) advect_batch_kernel(BatchArgs b) {
   __shared__ int tile;
   __shared__ StepArgs sa;
   unsigned long long done = 0;
@@ -293,7 +290,7 @@ __global__ void __launch_bounds__(256, SM ? 3 : 2) advect_batch_kernel(BatchArgs
     const int t = tile;
     if (t >= b.ntiles) break;
     const int64_t p = (int64_t)b.tiles[t].y + threadIdx.x;
-    if (p < sa.p.n && sa.p.status[p] == 0) done += advance_particle<float, Store, NF, D3, SM>(sa, p);
+    if (p < sa.p.n && sa.p.status[p] == 0) done += advance_particle<float, Store, NF, D3>(sa, p);
     __syncthreads();
   }
   count_steps(done, b.steps_done);

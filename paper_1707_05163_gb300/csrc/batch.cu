@@ -29,45 +29,44 @@ cudaError_t launch_resort(pg_pset *ps, cudaStream_t st, int64_t *n_alive);
 
 namespace {
 
-// The batch kernel for one (storage, shape, corner cache) choice: launch, or
-// report its occupancy.
-template <typename Store, int NF, bool D3, bool SM>
-cudaError_t batch_kernel_op(const BatchArgs *b, int block, int grid, cudaStream_t st, int *bps) {
-  auto kern = advect_batch_kernel<Store, NF, D3, SM>;
-  const size_t smem = SM ? corner_smem_bytes(NF, D3, block) : 0;
-  if (SM) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)corner_smem_bytes(NF, D3, 256));
-    if (e != cudaSuccess) return e;
-  }
-  if (bps) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, block, smem);
-  kern<<<grid, block, smem, st>>>(*b);
+template <typename Store>
+cudaError_t launch_batch_t(const BatchArgs &b, bool d3, int nf, int block, int grid,
+                           cudaStream_t st) {
+  if (nf == 3) advect_batch_kernel<Store, 3, true><<<grid, block, 0, st>>>(b);
+  else if (d3) advect_batch_kernel<Store, 2, true><<<grid, block, 0, st>>>(b);
+  else advect_batch_kernel<Store, 2, false><<<grid, block, 0, st>>>(b);
   note_launches(1);
   return cudaGetLastError();
 }
 
-template <typename Store, bool SM>
-cudaError_t batch_op_t(const BatchArgs *b, bool d3, int nf, int block, int grid, cudaStream_t st,
-                       int *bps) {
-  if (nf == 3) return batch_kernel_op<Store, 3, true, SM>(b, block, grid, st, bps);
-  if (d3) return batch_kernel_op<Store, 2, true, SM>(b, block, grid, st, bps);
-  return batch_kernel_op<Store, 2, false, SM>(b, block, grid, st, bps);
-}
-
 template <typename Store>
-cudaError_t batch_op_s(const BatchArgs *b, bool d3, int nf, int block, int grid, cudaStream_t st,
-                       int *bps, int cache) {
-  return cache ? batch_op_t<Store, true>(b, d3, nf, block, grid, st, bps)
-               : batch_op_t<Store, false>(b, d3, nf, block, grid, st, bps);
+cudaError_t occupancy_t(bool d3, int nf, int block, int *blocks_per_sm) {
+  if (nf == 3)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                         advect_batch_kernel<Store, 3, true>, block, 0);
+  if (d3)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                         advect_batch_kernel<Store, 2, true>, block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                       advect_batch_kernel<Store, 2, false>, block, 0);
 }
 
-cudaError_t batch_op(const pg_fieldset *fs, const BatchArgs *b, int block, int grid,
-                     cudaStream_t st, int *bps, int cache) {
+cudaError_t launch_batch(const BatchArgs &b, int storage, int block, int grid, cudaStream_t st) {
+  const bool d3 = b.g.nz > 1;
+  switch (storage) {
+    case PG_F32: return launch_batch_t<float>(b, d3, b.f.nf, block, grid, st);
+    case PG_F16S: return launch_batch_t<__half>(b, d3, b.f.nf, block, grid, st);
+    case PG_BF16S: return launch_batch_t<__nv_bfloat16>(b, d3, b.f.nf, block, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t batch_occupancy(const pg_fieldset *fs, int block, int *bps) {
   const bool d3 = fs->nz > 1;
   switch (fs->storage) {
-    case PG_F32: return batch_op_s<float>(b, d3, fs->nfields, block, grid, st, bps, cache);
-    case PG_F16S: return batch_op_s<__half>(b, d3, fs->nfields, block, grid, st, bps, cache);
-    case PG_BF16S: return batch_op_s<__nv_bfloat16>(b, d3, fs->nfields, block, grid, st, bps, cache);
+    case PG_F32: return occupancy_t<float>(d3, fs->nfields, block, bps);
+    case PG_F16S: return occupancy_t<__half>(d3, fs->nfields, block, bps);
+    case PG_BF16S: return occupancy_t<__nv_bfloat16>(d3, fs->nfields, block, bps);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -93,11 +92,11 @@ struct Batch {
 };
 
 // Enqueue windows [w0, w1) with the given block size and re-sort interval.
-cudaError_t enqueue_windows(Batch &B, int w0, int w1, int block, int resort_every, int cache,
+cudaError_t enqueue_windows(Batch &B, int w0, int w1, int block, int resort_every,
                             cudaStream_t st) {
   const pg_fieldset *fs = B.fs;
   int bps = 0;
-  cudaError_t e = batch_op(fs, nullptr, block, 0, st, &bps, cache);
+  cudaError_t e = batch_occupancy(fs, block, &bps);
   if (e != cudaSuccess) return e;
   const int grid = std::max(1, std::min(bps * fs->sm_count, B.ntiles));
   BatchArgs b;
@@ -113,7 +112,7 @@ cudaError_t enqueue_windows(Batch &B, int w0, int w1, int block, int resort_ever
   for (int w = w0; w < w1; ++w) {
     b.next_tile = B.d_next + w;
     b.t_stop = B.t_begin + (double)(w + 1) * B.window;
-    if ((e = batch_op(fs, &b, block, grid, st, nullptr, cache)) != cudaSuccess) return e;
+    if ((e = launch_batch(b, fs->storage, block, grid, st)) != cudaSuccess) return e;
     if (resort_every > 0 && (w + 1) % resort_every == 0 && w + 1 < B.nwin) {
       for (pg_pset *p : B.ps)
         if (p->n >= kResortMin && (e = launch_resort(p, st, nullptr)) != cudaSuccess) return e;
@@ -184,8 +183,7 @@ bool read_cache(const char *path, const std::string &key, pg_tune &t) {
   while (std::getline(f, line)) {
     const size_t bar = line.rfind('\t');
     if (bar == std::string::npos || line.substr(0, bar) != key) continue;
-    if (sscanf(line.c_str() + bar + 1, "%d %d %d", &t.block, &t.resort_steps, &t.cache) == 3)
-      return true;
+    if (sscanf(line.c_str() + bar + 1, "%d %d", &t.block, &t.resort_steps) == 2) return true;
   }
   return false;
 }
@@ -193,7 +191,7 @@ bool read_cache(const char *path, const std::string &key, pg_tune &t) {
 void write_cache(const char *path, const std::string &key, const pg_tune &t) {
   if (!path) return;
   std::ofstream f(path, std::ios::app);
-  f << key << '\t' << t.block << ' ' << t.resort_steps << ' ' << t.cache << '\n';
+  f << key << '\t' << t.block << ' ' << t.resort_steps << '\n';
 }
 
 }  // namespace
@@ -317,7 +315,7 @@ extern "C" pg_status pg_execute_batch(int nrel, pg_pset *const *psets,
     if (p->n >= kResortMin) CUB(prepare_resort(p));
 
   // ------------------------------------------------------------ autotune
-  pg_tune use{128, 1, 0, 0};
+  pg_tune use{128, 1, 0};
   if (tune) {
     use = *tune;
   } else {
@@ -328,24 +326,22 @@ extern "C" pg_status pg_execute_batch(int nrel, pg_pset *const *psets,
       const int trial = std::min(B.nwin, 4);
       const int blocks[] = {64, 128, 256};
       const int resorts[] = {0, 1, 2};
-      const int caches[] = {0, 1};
       float best = 1e30f;
       cudaEvent_t e0, e1;
       CUB(cudaEventCreate(&e0));
       CUB(cudaEventCreate(&e1));
-      for (int cache : caches)
       for (int bl : blocks)
         for (int rs : resorts) {
           if (build_tiles(bl)) { cudaEventDestroy(e0); cudaEventDestroy(e1); return PG_ERR_CUDA; }
           CUB(restore_state(B, bk, st));
           CUB(cudaMemsetAsync(B.d_next, 0, sizeof(int) * B.nwin, st));
           CUB(cudaEventRecord(e0, st));
-          CUB(enqueue_windows(B, 0, trial, bl, rs, cache, st));
+          CUB(enqueue_windows(B, 0, trial, bl, rs, st));
           CUB(cudaEventRecord(e1, st));
           CUB(cudaEventSynchronize(e1));
           float ms = 0.f;
           CUB(cudaEventElapsedTime(&ms, e0, e1));
-          if (ms < best) { best = ms; use.block = bl; use.resort_steps = rs; use.cache = cache; }
+          if (ms < best) { best = ms; use.block = bl; use.resort_steps = rs; }
         }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
@@ -372,7 +368,7 @@ extern "C" pg_status pg_execute_batch(int nrel, pg_pset *const *psets,
     CUB(cudaStreamWaitEvent(cap, ev, 0));
     cudaGraph_t graph = nullptr;
     CUB(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_windows(B, 0, B.nwin, use.block, use.resort_steps, use.cache, cap);
+    cudaError_t e = enqueue_windows(B, 0, B.nwin, use.block, use.resort_steps, cap);
     cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
@@ -397,7 +393,7 @@ extern "C" pg_status pg_execute_batch(int nrel, pg_pset *const *psets,
     }
     note_launches(0);
   } else {
-    CUB(enqueue_windows(B, 0, B.nwin, use.block, use.resort_steps, use.cache, st));
+    CUB(enqueue_windows(B, 0, B.nwin, use.block, use.resort_steps, st));
   }
   unsigned long long done = 0;
   int err = 0;

@@ -909,7 +909,6 @@ pg_status pg_pset_set_tune(pg_pset *ps, const pg_tune *tune) {
   ps->tune.block = tune->block ? tune->block : 256;
   ps->tune.resort_steps = tune->resort_steps;
   ps->tune.chunk_steps = tune->chunk_steps ? tune->chunk_steps : 64;
-  ps->tune.cache = tune->cache ? 1 : 0;
   return PG_OK;
 }
 
@@ -1067,10 +1066,8 @@ pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
     }
     a.p.ci = ps->ci; a.p.cj = ps->cj; a.p.ck = ps->ck;
     a.p.fx = ps->fx; a.p.fy = ps->fy; a.p.fz = ps->fz;
-    if (ps->pos == PG_POS_CELL)
-      CU(launch_advect_cell(a, fs->storage, ps->tune.block, st, ps->tune.cache));
-    else
-      CU(launch_advect_plain(a, ps->pos, fs->storage, ps->tune.block, st, ps->tune.cache));
+    if (ps->pos == PG_POS_CELL) CU(launch_advect_cell(a, fs->storage, ps->tune.block, st));
+    else CU(launch_advect_plain(a, ps->pos, fs->storage, ps->tune.block, st));
     if (ps->timing) {
       CU(cudaEventRecord(ps->ev[ps->ev_used + 1], st));
       ps->ev_used += 2;

@@ -108,7 +108,7 @@ struct pg_pset {
   uint32_t *step = nullptr;
   uint8_t *status = nullptr;
   double t_min = 0.0, t_max = 0.0;     // range of particle times
-  pg_tune tune{256, 0, 64, 0};
+  pg_tune tune{256, 0, 64};
   unsigned long long *d_counter = nullptr;
   int *d_err = nullptr;
   // re-sort: second set of arrays (same capacity) and scratch, on first use
@@ -133,11 +133,10 @@ cudaError_t launch_repack(const void *src, int src_dtype, int nf, size_t nodes, 
 
 // Advection chunk for lon/lat/depth positions.  real: PG_POS_F64 / PG_POS_F32.
 cudaError_t launch_advect_plain(const StepArgs &a, int real, int storage, int block,
-                                cudaStream_t st, int cache = 0);
+                                cudaStream_t st);
 
 // Advection chunk for cell-index + offset positions.
-cudaError_t launch_advect_cell(const StepArgs &a, int storage, int block, cudaStream_t st,
-                               int cache = 0);
+cudaError_t launch_advect_cell(const StepArgs &a, int storage, int block, cudaStream_t st);
 cudaError_t launch_to_cell(const GridArgs &g, const double *lon, const double *lat,
                            const double *dep, int32_t *ci, int32_t *cj, int32_t *ck, float *fx,
                            float *fy, float *fz, int64_t n, int sm, cudaStream_t st);
@@ -161,25 +160,18 @@ namespace pg {
 
 // Launch a chunk kernel over a.p.n particles, one thread each.  The block
 // size is clamped to what the kernel's register use allows.
-// smem_per_thread: dynamic shared memory per thread (corner cache), 0 if none.
 template <typename Kern>
-inline cudaError_t launch_clamped(Kern kernel, const StepArgs &a, int block, cudaStream_t st,
-                                  size_t smem_per_thread = 0) {
+inline cudaError_t launch_clamped(Kern kernel, const StepArgs &a, int block, cudaStream_t st) {
   static int max_threads = 0;
   if (max_threads == 0) {
     cudaFuncAttributes at;
-    cudaError_t e = cudaFuncGetAttributes(&at, kernel);
+    const cudaError_t e = cudaFuncGetAttributes(&at, kernel);
     if (e != cudaSuccess) return e;
     max_threads = at.maxThreadsPerBlock;
-    if (smem_per_thread) {
-      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(smem_per_thread * max_threads));
-      if (e != cudaSuccess) return e;
-    }
   }
   const int b = block > max_threads ? (max_threads / 32) * 32 : block;
   const int64_t grid = (a.p.n + b - 1) / b;
-  kernel<<<(unsigned)grid, b, smem_per_thread * b, st>>>(a);
+  kernel<<<(unsigned)grid, b, 0, st>>>(a);
   note_launches(1);
   return cudaGetLastError();
 }

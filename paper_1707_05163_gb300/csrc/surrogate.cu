@@ -403,7 +403,7 @@ pg_status pg_surrogate_run(pg_pset *ps, pg_mlp *net, const pg_kernel *k, int nst
     if (!q) q = pg_surrogate_apply(ps, y, horizon, st);
     return q;
   };
-  pg_tune keep_order{ps->tune.block > 0 ? ps->tune.block : 256, 0, 64, ps->tune.cache};
+  pg_tune keep_order{ps->tune.block > 0 ? ps->tune.block : 256, 0, 64};
   float ms_net = 0.f, ms_rk = 0.f;
   const auto t_start = std::chrono::steady_clock::now();
   int done_steps = 0;

@@ -186,38 +186,6 @@ def test_fp32_global_3d_within_cells(pg):
     assert g["steps"] == o["steps"]
 
 
-@pytest.mark.parametrize("pos,storage,nz", [("f32", "f32", 8), ("f32", "f16", 1),
-                                             ("cell", "bf16", 8), ("cell", "f32", 1)])
-def test_shared_memory_corner_cache_is_invisible(pg, pos, storage, nz):
-    """Keeping the cell corner values in shared memory instead of registers
-    changes where they live, not the arithmetic: trajectories are bit-identical,
-    and the 3-D FP32 case meets the same oracle bound as the register form."""
-    gf, spec = _small_global(nz=nz)
-    lon, lat, dep = synth.uniform_particles(3001, 9, (0, 360), (-70, 70), (6.0, 1000.0),
-                                            dtype=np.float32)
-    if nz == 1:
-        dep = None
-    fs = pg.FieldSet.from_spec(spec, storage=storage)
-    K = pg.Kernel("rk4", ("brownian",), kh=5.0)
-    T = 2.5 * DAY
-    got = []
-    for cache, block in ((0, 256), (1, 256), (1, 96)):
-        ps = pg.ParticleSet(fs, lon, lat, dep, pos=pos, seed=4)
-        ps.set_tune(block=block, chunk_steps=17, cache=cache)
-        got.append(gpu_run(ps, K, T, 1800.0))
-    for g in got[1:]:
-        for k in ("lon", "lat", "depth", "time", "step", "status"):
-            np.testing.assert_array_equal(g["final"][k], got[0]["final"][k], err_msg=k)
-        assert g["steps"] == got[0]["steps"]
-    if pos == "f32" and storage == "f32" and nz > 1:
-        o = oracle_run(oracle_field(spec), lon, lat, dep, 0.0, 1800.0, T,
-                       behaviours=("brownian",), kh=5.0, seed=4)
-        alive = o["final"]["status"] == 0
-        np.testing.assert_array_equal(got[1]["final"]["status"], o["final"]["status"])
-        e = cell_error(got[1]["final"], o["final"], spec)[alive]
-        assert np.mean(e) < 1e-3 and np.max(e) < 2e-2, (np.mean(e), np.max(e))
-
-
 @pytest.mark.parametrize("storage,kind", [("f16", 0), ("bf16", 1)])
 def test_quantised_storage_scales_and_trajectories(pg, storage, kind):
     gf, spec = _small_global(nz=1, res=1.0)
