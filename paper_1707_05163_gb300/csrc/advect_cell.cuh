@@ -42,14 +42,14 @@ __device__ __forceinline__ bool norm_axis(int &i, float &f, int n, bool periodic
 }
 
 // Velocity in cells per second at the stage position base + kc * off.
-template <typename Store, int NF, bool D3>
-__device__ __forceinline__ int velocity_cell(const StepArgs &a, Sampler<float, Store, NF, D3> &c,
+template <typename Store, int NF, bool D3, int GEO>
+__device__ __forceinline__ int velocity_cell(const StepArgs &a, Sampler<float, Store, NF, D3, GEO> &c,
                                              Clock &ck, float off, const CellState &b,
                                              const float (&kc)[3], float (&vel)[3]) {
   const GridArgs &g = a.g;
   int i = b.i, j = b.j, k = b.k;
   float x = b.x + kc[0] * off, y = b.y + kc[1] * off, z = D3 ? b.z + kc[2] * off : 0.f;
-  if (!norm_axis(i, x, g.nx, g.periodic)) return 1;
+  if (!norm_axis(i, x, g.nx, is_per<GEO>(g))) return 1;
   if (!norm_axis(j, y, g.ny, false)) return 1;
   if constexpr (D3) {
     if (!norm_axis(k, z, g.nz, false)) return 2;
@@ -60,7 +60,7 @@ __device__ __forceinline__ int velocity_cell(const StepArgs &a, Sampler<float, S
   c.ck = D3 ? k : 0;
   const int r = sample_fields(a, c, ck, off, x, y, z, vel);
   if (r) return r;
-  if (g.mesh == 1) {
+  if (is_sph<GEO>(g)) {
     const float lat = g.x0f[1] + ((float)j + y) * g.df[1];
     vel[0] = __fdividef(vel[0] * g.inv_m[0], cos_deg(lat));
   } else {
@@ -72,8 +72,8 @@ __device__ __forceinline__ int velocity_cell(const StepArgs &a, Sampler<float, S
 }
 
 // One step of Eq. 1 in cell units; the state is replaced only on success.
-template <typename Store, int NF, bool D3>
-__device__ __forceinline__ int step_cell(const StepArgs &a, Sampler<float, Store, NF, D3> &c,
+template <typename Store, int NF, bool D3, int GEO>
+__device__ __forceinline__ int step_cell(const StepArgs &a, Sampler<float, Store, NF, D3, GEO> &c,
                                          Clock &ck, CellState &s, float h, uint64_t id,
                                          uint32_t stp) {
   const GridArgs &g = a.g;
@@ -104,12 +104,12 @@ __device__ __forceinline__ int step_cell(const StepArgs &a, Sampler<float, Store
     normal_pair(a.k.seed, id, stp, n1, n2);
     const float sigma = sqrtf(2.f * a.k.kh_f * fabsf(h));
     float dx = sigma * n1 * g.inv_m[0];
-    if (g.mesh == 1) dx = __fdividef(dx, cos_deg(g.x0f[1] + ((float)n.j + n.y) * g.df[1]));
+    if (is_sph<GEO>(g)) dx = __fdividef(dx, cos_deg(g.x0f[1] + ((float)n.j + n.y) * g.df[1]));
     n.x += dx;
     n.y += sigma * n2 * g.inv_m[1];
   }
   if (D3 && (a.k.beh & 2u)) n.z += a.k.w_sink_f * h * g.inv_m[2];
-  if (!norm_axis(n.i, n.x, g.nx, g.periodic)) return 1;
+  if (!norm_axis(n.i, n.x, g.nx, is_per<GEO>(g))) return 1;
   if (!norm_axis(n.j, n.y, g.ny, false)) return 1;
   if constexpr (D3) {
     if (!norm_axis(n.k, n.z, g.nz, false)) return 2;
@@ -118,7 +118,7 @@ __device__ __forceinline__ int step_cell(const StepArgs &a, Sampler<float, Store
   return 0;
 }
 
-template <typename Store, int NF, bool D3>
+template <typename Store, int NF, bool D3, int GEO>
 __global__ void __launch_bounds__(256, 2) advect_cell_kernel(StepArgs a) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long done = 0;
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256, 2) advect_cell_kernel(StepArgs a) {
     uint32_t stp = a.p.step[p];
     const uint64_t id = a.p.id[p];
     uint8_t st = 0;
-    Sampler<float, Store, NF, D3> c;
+    Sampler<float, Store, NF, D3, GEO> c;
     c.reset();
     const double sgn = a.dt > 0.0 ? 1.0 : -1.0;
     // the step count of this chunk is fixed up front; step k starts at

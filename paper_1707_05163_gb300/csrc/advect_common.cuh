@@ -127,7 +127,7 @@ __device__ __forceinline__ int axis_search(const GridArgs &g, int a, int n, Real
 }
 
 // ---------------------------------------------------------- the sampler ---
-template <typename Real, typename Store, int NF, bool D3>
+template <typename Real, typename Store, int NF, bool D3, int GEO = GEO_ANY>
 struct Sampler {
   static constexpr int NC = D3 ? 8 : 4;
   // cached cell (ci = -1: none) and its bounds
@@ -210,8 +210,8 @@ __device__ __forceinline__ bool time_interval(const FieldArgs &f, double t, int 
   return true;
 }
 
-template <typename Real, typename Store, int NF, bool D3>
-__device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
+template <typename Real, typename Store, int NF, bool D3, int GEO>
+__device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                             int sl, int s) {
   const GridArgs &g = a.g;
   const Store *base = reinterpret_cast<const Store *>(a.f.tab[s]);
@@ -244,8 +244,8 @@ __device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Sto
 // Make `v` hold the corners of the cached cell for snapshots s0 and s1.  If
 // only the snapshot pair moved on by one, the shared snapshot's corners move
 // from slot 1 to slot 0 and only the new snapshot is read.
-template <typename Real, typename Store, int NF, bool D3>
-__device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
+template <typename Real, typename Store, int NF, bool D3, int GEO>
+__device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                        bool steady) {
   const bool same_cell = c.gi == c.ci && c.gj == c.cj && c.gk == c.ck && c.gi >= 0;
   if (steady) {
@@ -254,7 +254,7 @@ __device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, N
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
-      for (int q = 0; q < Sampler<Real, Store, NF, D3>::NC; ++q) c.v[0][f][q] = c.v[1][f][q];
+      for (int q = 0; q < Sampler<Real, Store, NF, D3, GEO>::NC; ++q) c.v[0][f][q] = c.v[1][f][q];
     if (!gather_slab(a, c, 1, c.s1)) return false;
   } else {
     if (!gather_slab(a, c, 0, c.s0)) return false;
@@ -292,13 +292,13 @@ struct Clock {
   __device__ __forceinline__ double start() const { return t + (double)k * dt; }
 };
 
-template <typename Real>
+template <typename Real, int GEO>
 __device__ __forceinline__ int out_of_domain(const GridArgs &g, Real lon, Real lat, Real dep,
                                              bool d3) {
   const Real *X = axis<Real>(g, 0);
   const Real *Y = axis<Real>(g, 1);
-  if (!g.periodic && !(lon >= X[0] && lon <= X[g.nx - 1])) return 1;
-  if (g.periodic && !(lon == lon)) return 1;
+  if (!is_per<GEO>(g) && !(lon >= X[0] && lon <= X[g.nx - 1])) return 1;
+  if (is_per<GEO>(g) && !(lon == lon)) return 1;
   if (!(lat >= Y[0] && lat <= Y[g.ny - 1])) return 1;
   if (d3) {
     const Real *Z = axis<Real>(g, 2);
@@ -317,8 +317,8 @@ __device__ __forceinline__ float w_of(const KernArgs &k, float) { return k.w_sin
 // (step start + off), corner gather if the cell or interval changed, spatial
 // interpolation in each snapshot, then linear interpolation in time.
 // Returns 0, PG_NAN (3), or -1 for an internal failure recorded in a.err.
-template <typename Real, typename Store, int NF, bool D3>
-__device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
+template <typename Real, typename Store, int NF, bool D3, int GEO>
+__device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                              Clock &ck, Real off, Real xi, Real eta, Real zeta,
                                              Real (&vel)[3]) {
   const bool steady = a.f.nt == 1;
@@ -363,9 +363,9 @@ __device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, St
   }
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    Real val = interp_space<Real, Sampler<Real, Store, NF, D3>::NC>(c.v[0][f], xi, eta, zeta);
+    Real val = interp_space<Real, Sampler<Real, Store, NF, D3, GEO>::NC>(c.v[0][f], xi, eta, zeta);
     if (!steady) {
-      const Real b = interp_space<Real, Sampler<Real, Store, NF, D3>::NC>(c.v[1][f], xi, eta, zeta);
+      const Real b = interp_space<Real, Sampler<Real, Store, NF, D3, GEO>::NC>(c.v[1][f], xi, eta, zeta);
       // FP64: the definition's a + (b - a) tau.  FP32: (1 - tau) a + tau b,
       // exact at both ends, so a stage time on a snapshot gives the same
       // value from either neighbouring interval (results do not depend on

@@ -7,13 +7,21 @@ namespace pg {
 
 cudaError_t launch_advect_f64(const StepArgs &a, int storage, int block, cudaStream_t st);
 
+template <typename Store, int GEO>
+static cudaError_t launch_geo(const StepArgs &a, int block, cudaStream_t st) {
+  if (a.f.nf == 3) return launch_clamped<advect_plain_kernel<float, Store, 3, true, GEO>>(a, block, st);
+  if (a.g.nz > 1) return launch_clamped<advect_plain_kernel<float, Store, 2, true, GEO>>(a, block, st);
+  return launch_clamped<advect_plain_kernel<float, Store, 2, false, GEO>>(a, block, st);
+}
+
 template <typename Store>
 static cudaError_t launch_f32(const StepArgs &a, int block, cudaStream_t st) {
   if (a.p.n == 0) return cudaSuccess;
-  const bool d3 = a.g.nz > 1;
-  if (a.f.nf == 3) return launch_clamped(advect_plain_kernel<float, Store, 3, true>, a, block, st);
-  if (d3) return launch_clamped(advect_plain_kernel<float, Store, 2, true>, a, block, st);
-  return launch_clamped(advect_plain_kernel<float, Store, 2, false>, a, block, st);
+  switch (geo_of(a.g)) {
+    case GEO_FLAT: return launch_geo<Store, GEO_FLAT>(a, block, st);
+    case GEO_SPH: return launch_geo<Store, GEO_SPH>(a, block, st);
+    default: return launch_geo<Store, GEO_SPH_PER>(a, block, st);
+  }
 }
 
 cudaError_t launch_advect_plain(const StepArgs &a, int real, int storage, int block,

@@ -9,10 +9,11 @@ namespace pg {
 template <typename Store>
 static cudaError_t launch_f64(const StepArgs &a, int block, cudaStream_t st) {
   if (a.p.n == 0) return cudaSuccess;
-  const bool d3 = a.g.nz > 1;
-  if (a.f.nf == 3) return launch_clamped(advect_plain_kernel<double, Store, 3, true>, a, block, st);
-  if (d3) return launch_clamped(advect_plain_kernel<double, Store, 2, true>, a, block, st);
-  return launch_clamped(advect_plain_kernel<double, Store, 2, false>, a, block, st);
+  if (a.f.nf == 3)
+    return launch_clamped<advect_plain_kernel<double, Store, 3, true, GEO_ANY>>(a, block, st);
+  if (a.g.nz > 1)
+    return launch_clamped<advect_plain_kernel<double, Store, 2, true, GEO_ANY>>(a, block, st);
+  return launch_clamped<advect_plain_kernel<double, Store, 2, false, GEO_ANY>>(a, block, st);
 }
 
 cudaError_t launch_advect_f64(const StepArgs &a, int storage, int block, cudaStream_t st) {

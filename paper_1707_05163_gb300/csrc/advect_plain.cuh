@@ -26,19 +26,19 @@ namespace pg {
 
 // Locate p on the longitude axis, using and refreshing the cache.
 // Returns false when the position is out of the domain.
-template <typename Real, typename Store, int NF, bool D3>
-__device__ __forceinline__ bool locate_lon(const GridArgs &g, Sampler<Real, Store, NF, D3> &c,
+template <typename Real, typename Store, int NF, bool D3, int GEO>
+__device__ __forceinline__ bool locate_lon(const GridArgs &g, Sampler<Real, Store, NF, D3, GEO> &c,
                                            Real p, Real &xi) {
   Real q = p;
   const Real *x = axis<Real>(g, 0);
-  if (g.periodic) {
+  if (is_per<GEO>(g)) {
     if (!isfinite(p)) return false;
     q = wrap_lon(p, x[0]);
   } else if (!(p >= x[0] && p <= x[g.nx - 1])) {
     return false;
   }
-  if (!(c.ci >= 0 && in_cell<Real>(q, c.xlo, c.xhi, c.ci == g.nx - 2 && !g.periodic))) {
-    if (g.periodic && q >= x[g.nx - 1]) {
+  if (!(c.ci >= 0 && in_cell<Real>(q, c.xlo, c.xhi, c.ci == g.nx - 2 && !is_per<GEO>(g)))) {
+    if (is_per<GEO>(g) && q >= x[g.nx - 1]) {
       c.ci = g.nx - 1; c.ci1 = 0;
       c.xlo = x[g.nx - 1];
       c.xhi = lon_end(g, p);
@@ -72,8 +72,8 @@ __device__ __forceinline__ bool locate_axis(const GridArgs &g, int a, int n, int
 // Velocity in position units per second at a stage (stage time = step start
 // + off).  Returns 0 or a particle status (PG_OOB_*, PG_NAN); -1 for an
 // internal failure already recorded in a.err.
-template <typename Real, typename Store, int NF, bool D3>
-__device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
+template <typename Real, typename Store, int NF, bool D3, int GEO>
+__device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                         Clock &ck, Real off, Real lon, Real lat, Real dep,
                                         Real (&vel)[3]) {
   const GridArgs &g = a.g;
@@ -87,7 +87,7 @@ __device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, 
   }
   const int r = sample_fields(a, c, ck, off, xi, eta, zeta, vel);
   if (r) return r;
-  if (g.mesh == 1) {
+  if (is_sph<GEO>(g)) {
     vel[0] = lon_rate(vel[0], lat, a.k);
     vel[1] = lat_rate(vel[1], a.k);
   }
@@ -97,8 +97,8 @@ __device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, 
 // One step of Eq. 1.  Returns 0 and updates (lon, lat, dep) on success.
 // RK4 stages run in a loop: stage s samples at (X + k_{s-1} c_s h, t + c_s h)
 // with c = (0, 1/2, 1/2, 1) and accumulates ((k1 + 2 k2) + 2 k3) + k4.
-template <typename Real, typename Store, int NF, bool D3>
-__device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, NF, D3> &c,
+template <typename Real, typename Store, int NF, bool D3, int GEO>
+__device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                         Clock &ck, Real &lon, Real &lat, Real &dep, Real hr,
                                         uint64_t id, uint32_t stp) {
   Real kc[3] = {(Real)0, (Real)0, (Real)0};
@@ -141,7 +141,7 @@ __device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, 
     normal_pair(a.k.seed, id, stp, n1, n2);
     const Real sigma = pg_sqrt((Real)2 * kh_of(a.k, hr) * pg_fabs(hr));
     Real dx = sigma * n1, dy = sigma * n2;
-    if (a.g.mesh == 1) {
+    if (is_sph<GEO>(a.g)) {
       dx = lon_rate(dx, nlat, a.k);
       dy = lat_rate(dy, a.k);
     }
@@ -149,8 +149,8 @@ __device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, 
     nlat = nlat + dy;
   }
   if (a.k.beh & 2u) ndep = ndep + w_of(a.k, hr) * hr;
-  if (a.g.periodic) nlon = wrap_lon(nlon, axis<Real>(a.g, 0)[0]);
-  if ((r = out_of_domain<Real>(a.g, nlon, nlat, ndep, D3))) return r;
+  if (is_per<GEO>(a.g)) nlon = wrap_lon(nlon, axis<Real>(a.g, 0)[0]);
+  if ((r = out_of_domain<Real, GEO>(a.g, nlon, nlat, ndep, D3))) return r;
   lon = nlon; lat = nlat; dep = ndep;
   return 0;
 }
@@ -158,7 +158,7 @@ __device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, 
 // The chunk kernel: each thread advances one particle while its time is
 // before t_stop and t_end (in the direction of dt), shortening only the step
 // that lands on t_end.  Returns the number of steps taken.
-template <typename Real, typename Store, int NF, bool D3>
+template <typename Real, typename Store, int NF, bool D3, int GEO>
 __device__ __forceinline__ unsigned long long advance_particle(const StepArgs &a, int64_t p) {
   unsigned long long done = 0;
   {
@@ -170,7 +170,7 @@ __device__ __forceinline__ unsigned long long advance_particle(const StepArgs &a
     uint32_t stp = a.p.step[p];
     const uint64_t id = a.p.id[p];
     uint8_t st = 0;
-    Sampler<Real, Store, NF, D3> c;
+    Sampler<Real, Store, NF, D3, GEO> c;
     c.reset();
     const double sgn = a.dt > 0.0 ? 1.0 : -1.0;
     Clock ck;
@@ -232,11 +232,11 @@ __device__ __forceinline__ void count_steps(unsigned long long done, unsigned lo
 // FP32: at most 128 registers (two 256-thread blocks per SM); measured
 // faster than the unbounded allocation despite a few spilled words, as more
 // resident warps hide the gather and dependency latencies.
-template <typename Real, typename Store, int NF, bool D3>
+template <typename Real, typename Store, int NF, bool D3, int GEO>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1) advect_plain_kernel(StepArgs a) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long done = 0;
-  if (p < a.p.n && a.p.status[p] == 0) done = advance_particle<Real, Store, NF, D3>(a, p);
+  if (p < a.p.n && a.p.status[p] == 0) done = advance_particle<Real, Store, NF, D3, GEO>(a, p);
   count_steps(done, a.steps_done);
 }
 
@@ -265,7 +265,7 @@ struct BatchArgs {
 
 // The argument block of the current tile's release is assembled once per
 // tile in shared memory, which every thread of the tile then reads.
-template <typename Store, int NF, bool D3>
+template <typename Store, int NF, bool D3, int GEO>
 __global__ void __launch_bounds__(256, 2) advect_batch_kernel(BatchArgs b) {
   __shared__ int tile;
   __shared__ StepArgs sa;
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(256, 2) advect_batch_kernel(BatchArgs b) {
     const int t = tile;
     if (t >= b.ntiles) break;
     const int64_t p = (int64_t)b.tiles[t].y + threadIdx.x;
-    if (p < sa.p.n && sa.p.status[p] == 0) done += advance_particle<float, Store, NF, D3>(sa, p);
+    if (p < sa.p.n && sa.p.status[p] == 0) done += advance_particle<float, Store, NF, D3, GEO>(sa, p);
     __syncthreads();
   }
   count_steps(done, b.steps_done);

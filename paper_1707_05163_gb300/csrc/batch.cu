@@ -29,44 +29,34 @@ cudaError_t launch_resort(pg_pset *ps, cudaStream_t st, int64_t *n_alive);
 
 namespace {
 
-template <typename Store>
-cudaError_t launch_batch_t(const BatchArgs &b, bool d3, int nf, int block, int grid,
-                           cudaStream_t st) {
-  if (nf == 3) advect_batch_kernel<Store, 3, true><<<grid, block, 0, st>>>(b);
-  else if (d3) advect_batch_kernel<Store, 2, true><<<grid, block, 0, st>>>(b);
-  else advect_batch_kernel<Store, 2, false><<<grid, block, 0, st>>>(b);
+// The batch kernel for one field shape and geometry: launch it (bps null) or
+// report its occupancy in blocks per SM.
+template <typename Store, int GEO>
+cudaError_t batch_geo(const BatchArgs &b, int block, int grid, cudaStream_t st, int *bps) {
+  auto kern = b.f.nf == 3 ? advect_batch_kernel<Store, 3, true, GEO>
+            : (b.g.nz > 1 ? advect_batch_kernel<Store, 2, true, GEO>
+                          : advect_batch_kernel<Store, 2, false, GEO>);
+  if (bps) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, block, 0);
+  kern<<<grid, block, 0, st>>>(b);
   note_launches(1);
   return cudaGetLastError();
 }
 
 template <typename Store>
-cudaError_t occupancy_t(bool d3, int nf, int block, int *blocks_per_sm) {
-  if (nf == 3)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
-                                                         advect_batch_kernel<Store, 3, true>, block, 0);
-  if (d3)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
-                                                         advect_batch_kernel<Store, 2, true>, block, 0);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
-                                                       advect_batch_kernel<Store, 2, false>, block, 0);
-}
-
-cudaError_t launch_batch(const BatchArgs &b, int storage, int block, int grid, cudaStream_t st) {
-  const bool d3 = b.g.nz > 1;
-  switch (storage) {
-    case PG_F32: return launch_batch_t<float>(b, d3, b.f.nf, block, grid, st);
-    case PG_F16S: return launch_batch_t<__half>(b, d3, b.f.nf, block, grid, st);
-    case PG_BF16S: return launch_batch_t<__nv_bfloat16>(b, d3, b.f.nf, block, grid, st);
-    default: return cudaErrorInvalidValue;
+cudaError_t batch_store(const BatchArgs &b, int block, int grid, cudaStream_t st, int *bps) {
+  switch (geo_of(b.g)) {
+    case GEO_FLAT: return batch_geo<Store, GEO_FLAT>(b, block, grid, st, bps);
+    case GEO_SPH: return batch_geo<Store, GEO_SPH>(b, block, grid, st, bps);
+    default: return batch_geo<Store, GEO_SPH_PER>(b, block, grid, st, bps);
   }
 }
 
-cudaError_t batch_occupancy(const pg_fieldset *fs, int block, int *bps) {
-  const bool d3 = fs->nz > 1;
-  switch (fs->storage) {
-    case PG_F32: return occupancy_t<float>(d3, fs->nfields, block, bps);
-    case PG_F16S: return occupancy_t<__half>(d3, fs->nfields, block, bps);
-    case PG_BF16S: return occupancy_t<__nv_bfloat16>(d3, fs->nfields, block, bps);
+cudaError_t batch_op(const BatchArgs &b, int storage, int block, int grid, cudaStream_t st,
+                     int *bps) {
+  switch (storage) {
+    case PG_F32: return batch_store<float>(b, block, grid, st, bps);
+    case PG_F16S: return batch_store<__half>(b, block, grid, st, bps);
+    case PG_BF16S: return batch_store<__nv_bfloat16>(b, block, grid, st, bps);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -95,10 +85,6 @@ struct Batch {
 cudaError_t enqueue_windows(Batch &B, int w0, int w1, int block, int resort_every,
                             cudaStream_t st) {
   const pg_fieldset *fs = B.fs;
-  int bps = 0;
-  cudaError_t e = batch_occupancy(fs, block, &bps);
-  if (e != cudaSuccess) return e;
-  const int grid = std::max(1, std::min(bps * fs->sm_count, B.ntiles));
   BatchArgs b;
   b.g = grid_args_of(fs);
   b.f.nt = fs->nt; b.f.nf = fs->nfields; b.f.times = fs->d_times; b.f.period = fs->period;
@@ -109,10 +95,14 @@ cudaError_t enqueue_windows(Batch &B, int w0, int w1, int block, int resort_ever
   b.ntiles = B.ntiles;
   b.steps_done = B.d_steps;
   b.err = B.d_err;
+  int bps = 0;
+  cudaError_t e = batch_op(b, fs->storage, block, 0, st, &bps);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(bps * fs->sm_count, B.ntiles));
   for (int w = w0; w < w1; ++w) {
     b.next_tile = B.d_next + w;
     b.t_stop = B.t_begin + (double)(w + 1) * B.window;
-    if ((e = launch_batch(b, fs->storage, block, grid, st)) != cudaSuccess) return e;
+    if ((e = batch_op(b, fs->storage, block, grid, st, nullptr)) != cudaSuccess) return e;
     if (resort_every > 0 && (w + 1) % resort_every == 0 && w + 1 < B.nwin) {
       for (pg_pset *p : B.ps)
         if (p->n >= kResortMin && (e = launch_resort(p, st, nullptr)) != cudaSuccess) return e;

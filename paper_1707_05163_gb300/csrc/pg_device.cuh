@@ -63,6 +63,21 @@ struct PartArgs {
   uint8_t *status;
 };
 
+// Mesh geometry of a kernel instantiation: runtime (GEO_ANY, the FP64 path)
+// or fixed at compile time (the FP32 kernels, one instantiation per kind), so
+// the per-stage mesh and wrap tests cost nothing.  A periodic zonal boundary
+// needs a spherical mesh, so these three kinds cover every field set.
+enum : int { GEO_ANY = 0, GEO_FLAT = 1, GEO_SPH = 2, GEO_SPH_PER = 3 };
+
+template <int GEO> __device__ __forceinline__ bool is_sph(const GridArgs &g) {
+  if constexpr (GEO == GEO_ANY) return g.mesh == 1;
+  else return GEO != GEO_FLAT;
+}
+template <int GEO> __device__ __forceinline__ bool is_per(const GridArgs &g) {
+  if constexpr (GEO == GEO_ANY) return g.periodic != 0;
+  else return GEO == GEO_SPH_PER;
+}
+
 struct StepArgs {
   GridArgs g;
   FieldArgs f;

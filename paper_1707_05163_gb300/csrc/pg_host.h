@@ -158,20 +158,26 @@ inline size_t storage_elem(int storage) {
 
 namespace pg {
 
+// Geometry kind of a grid; the FP32 kernels are compiled once per kind.
+inline int geo_of(const GridArgs &g) {
+  return g.mesh != 1 ? GEO_FLAT : (g.periodic ? GEO_SPH_PER : GEO_SPH);
+}
+
 // Launch a chunk kernel over a.p.n particles, one thread each.  The block
-// size is clamped to what the kernel's register use allows.
-template <typename Kern>
-inline cudaError_t launch_clamped(Kern kernel, const StepArgs &a, int block, cudaStream_t st) {
+// size is clamped to what the kernel's register use allows (queried once per
+// kernel).
+template <void (*Kernel)(StepArgs)>
+inline cudaError_t launch_clamped(const StepArgs &a, int block, cudaStream_t st) {
   static int max_threads = 0;
   if (max_threads == 0) {
     cudaFuncAttributes at;
-    const cudaError_t e = cudaFuncGetAttributes(&at, kernel);
+    const cudaError_t e = cudaFuncGetAttributes(&at, Kernel);
     if (e != cudaSuccess) return e;
     max_threads = at.maxThreadsPerBlock;
   }
   const int b = block > max_threads ? (max_threads / 32) * 32 : block;
   const int64_t grid = (a.p.n + b - 1) / b;
-  kernel<<<(unsigned)grid, b, 0, st>>>(a);
+  Kernel<<<(unsigned)grid, b, 0, st>>>(a);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -186,6 +186,40 @@ def test_fp32_global_3d_within_cells(pg):
     assert g["steps"] == o["steps"]
 
 
+@pytest.mark.parametrize("geo", ["flat", "sphere_regional", "sphere_coarse_lat"])
+def test_fp32_each_mesh_geometry(pg, geo):
+    """The FP32 kernels are compiled once per geometry (flat; spherical;
+    spherical with a periodic zonal boundary).  Each kind against the oracle,
+    the spherical ones on a 1-degree regional grid and on a coarse global grid
+    with 12-degree cells."""
+    import dataclasses
+    if geo == "flat":
+        spec = synth.stommel_gyre(n=101)
+        rng = np.random.default_rng(31)
+        lon = rng.uniform(1e5, 9e5, 3000).astype(np.float32)
+        lat = rng.uniform(1e5, 9e5, 3000).astype(np.float32)
+        dt, T = 3600.0, 20 * DAY
+    else:
+        gf, spec = _small_global(nz=1, res=12.0 if geo == "sphere_coarse_lat" else 1.0)
+        if geo == "sphere_regional":
+            keep = spec.lon <= 120.0
+            spec = dataclasses.replace(spec, lon=spec.lon[keep], data=spec.data[..., keep],
+                                       periodic_lon=False)
+        lon, lat, _ = synth.uniform_particles(3000, 11, (spec.lon[0], spec.lon[-1]),
+                                              (spec.lat[0], spec.lat[-1]), dtype=np.float32)
+        dt, T = 1800.0, 3 * DAY
+    o = oracle_run(oracle_field(spec), lon, lat, None, 0.0, dt, T)
+    fs = pg.FieldSet.from_spec(spec, storage="f32")
+    ps = pg.ParticleSet(fs, lon, lat, pos="f32")
+    g = gpu_run(ps, pg.Kernel("rk4"), T, dt)
+    np.testing.assert_array_equal(g["final"]["status"], o["final"]["status"])
+    alive = o["final"]["status"] == 0
+    assert alive.sum() > 1000
+    e = cell_error(g["final"], o["final"], spec, periodic=spec.periodic_lon)[alive]
+    assert np.mean(e) < 1e-3 and np.max(e) < 2e-2, (np.mean(e), np.max(e))
+    assert g["steps"] == o["steps"]
+
+
 @pytest.mark.parametrize("storage,kind", [("f16", 0), ("bf16", 1)])
 def test_quantised_storage_scales_and_trajectories(pg, storage, kind):
     gf, spec = _small_global(nz=1, res=1.0)
