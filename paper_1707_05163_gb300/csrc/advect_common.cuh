@@ -100,6 +100,10 @@ template <> __device__ __forceinline__ float axis_x0<float>(const GridArgs &g, i
 template <typename Real> __device__ __forceinline__ Real axis_inv(const GridArgs &g, int a);
 template <> __device__ __forceinline__ double axis_inv<double>(const GridArgs &g, int a) { return g.inv_d[a]; }
 template <> __device__ __forceinline__ float axis_inv<float>(const GridArgs &g, int a) { return g.inv_df[a]; }
+__device__ __forceinline__ double axis_lo(const GridArgs &g, int a, double) { return g.lo[a]; }
+__device__ __forceinline__ float axis_lo(const GridArgs &g, int a, float) { return g.lof[a]; }
+__device__ __forceinline__ double axis_hi(const GridArgs &g, int a, double) { return g.hi[a]; }
+__device__ __forceinline__ float axis_hi(const GridArgs &g, int a, float) { return g.hif[a]; }
 __device__ __forceinline__ double lon_end(const GridArgs &g, double) { return g.lon_end; }
 __device__ __forceinline__ float lon_end(const GridArgs &g, float) { return g.lon_end_f; }
 
@@ -186,8 +190,11 @@ __device__ __forceinline__ bool time_interval(const FieldArgs &f, double t, int 
   const int nt = f.nt;
   tt = t;
   if (f.period > 0.0) {
-    double r = fmod(t - T[0], f.period);
-    if (r < 0.0) r += f.period;
+    double r = t - T[0];
+    if (!(r >= 0.0 && r < f.period)) {   // fmod is the identity on [0, period)
+      r = fmod(r, f.period);
+      if (r < 0.0) r += f.period;
+    }
     tt = T[0] + r;
     if (tt >= T[nt - 1]) {
       s0 = nt - 1; s1 = 0;
@@ -250,6 +257,12 @@ __device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, N
   const bool same_cell = c.gi == c.ci && c.gj == c.cj && c.gk == c.ck && c.gi >= 0;
   if (steady) {
     if (!gather_slab(a, c, 0, c.s0)) return false;
+    if constexpr (sizeof(Real) == 4) {     // FP32 interpolates both slots
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int q = 0; q < Sampler<Real, Store, NF, D3, GEO>::NC; ++q) c.v[1][f][q] = c.v[0][f][q];
+    }
   } else if (same_cell && c.s0 == c.gs1) {
 #pragma unroll
     for (int f = 0; f < NF; ++f)
@@ -295,15 +308,11 @@ struct Clock {
 template <typename Real, int GEO>
 __device__ __forceinline__ int out_of_domain(const GridArgs &g, Real lon, Real lat, Real dep,
                                              bool d3) {
-  const Real *X = axis<Real>(g, 0);
-  const Real *Y = axis<Real>(g, 1);
-  if (!is_per<GEO>(g) && !(lon >= X[0] && lon <= X[g.nx - 1])) return 1;
+  const Real z = (Real)0;
+  if (!is_per<GEO>(g) && !(lon >= axis_lo(g, 0, z) && lon <= axis_hi(g, 0, z))) return 1;
   if (is_per<GEO>(g) && !(lon == lon)) return 1;
-  if (!(lat >= Y[0] && lat <= Y[g.ny - 1])) return 1;
-  if (d3) {
-    const Real *Z = axis<Real>(g, 2);
-    if (!(dep >= Z[0] && dep <= Z[g.nz - 1])) return 2;
-  }
+  if (!(lat >= axis_lo(g, 1, z) && lat <= axis_hi(g, 1, z))) return 1;
+  if (d3 && !(dep >= axis_lo(g, 2, z) && dep <= axis_hi(g, 2, z))) return 2;
   return 0;
 }
 
@@ -361,19 +370,27 @@ __device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, St
       c.gi < 0) {
     if (!gather(a, c, steady)) return -1;
   }
+  constexpr int NC = Sampler<Real, Store, NF, D3, GEO>::NC;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    Real val = interp_space<Real, Sampler<Real, Store, NF, D3, GEO>::NC>(c.v[0][f], xi, eta, zeta);
-    if (!steady) {
-      const Real b = interp_space<Real, Sampler<Real, Store, NF, D3, GEO>::NC>(c.v[1][f], xi, eta, zeta);
-      // FP64: the definition's a + (b - a) tau.  FP32: (1 - tau) a + tau b,
-      // exact at both ends, so a stage time on a snapshot gives the same
-      // value from either neighbouring interval (results do not depend on
-      // which interval a thread happens to have cached).
-      if constexpr (sizeof(Real) == 8) val = val + (b - val) * tau;
-      else val = fmaf(tau, b, (1.0f - tau) * val);
+    Real val = interp_space<Real, NC>(c.v[0][f], xi, eta, zeta);
+    if constexpr (sizeof(Real) == 8) {
+      // the definition's a + (b - a) tau, and its NaN test per value
+      if (!steady) {
+        const Real b = interp_space<Real, NC>(c.v[1][f], xi, eta, zeta);
+        val = val + (b - val) * tau;
+      }
+      if (!(val == val)) return 3;
+    } else {
+      // (1 - tau) a + tau b, exact at both ends, so a stage time on a
+      // snapshot gives the same value from either neighbouring interval
+      // (results do not depend on which interval a thread has cached).  A
+      // steady field holds its snapshot in both slots with tau = 0, which
+      // returns a exactly, so the path has no branch on steadiness here.
+      const Real b = interp_space<Real, NC>(c.v[1][f], xi, eta, zeta);
+      val = fmaf(tau, b, (1.0f - tau) * val);
+      if (!(val == val)) return 3;
     }
-    if (!(val == val)) return 3;
     vel[f] = val;
   }
   if constexpr (NF == 2) vel[2] = (Real)0;

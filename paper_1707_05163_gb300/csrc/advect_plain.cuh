@@ -33,12 +33,12 @@ __device__ __forceinline__ bool locate_lon(const GridArgs &g, Sampler<Real, Stor
   const Real *x = axis<Real>(g, 0);
   if (is_per<GEO>(g)) {
     if (!isfinite(p)) return false;
-    q = wrap_lon(p, x[0]);
-  } else if (!(p >= x[0] && p <= x[g.nx - 1])) {
+    q = wrap_lon(p, axis_lo(g, 0, p));
+  } else if (!(p >= axis_lo(g, 0, p) && p <= axis_hi(g, 0, p))) {
     return false;
   }
   if (!(c.ci >= 0 && in_cell<Real>(q, c.xlo, c.xhi, c.ci == g.nx - 2 && !is_per<GEO>(g)))) {
-    if (is_per<GEO>(g) && q >= x[g.nx - 1]) {
+    if (is_per<GEO>(g) && q >= axis_hi(g, 0, p)) {
       c.ci = g.nx - 1; c.ci1 = 0;
       c.xlo = x[g.nx - 1];
       c.xhi = lon_end(g, p);
@@ -149,7 +149,7 @@ __device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, 
     nlat = nlat + dy;
   }
   if (a.k.beh & 2u) ndep = ndep + w_of(a.k, hr) * hr;
-  if (is_per<GEO>(a.g)) nlon = wrap_lon(nlon, axis<Real>(a.g, 0)[0]);
+  if (is_per<GEO>(a.g)) nlon = wrap_lon(nlon, axis_lo(a.g, 0, nlon));
   if ((r = out_of_domain<Real, GEO>(a.g, nlon, nlat, ndep, D3))) return r;
   lon = nlon; lat = nlat; dep = ndep;
   return 0;

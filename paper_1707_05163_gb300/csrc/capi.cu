@@ -239,6 +239,11 @@ GridArgs grid_args(const pg_fieldset *fs) {
   }
   g.lon_end = fs->lon[0] + 360.0;
   g.lon_end_f = (float)g.lon_end;
+  for (int a = 0; a < 3; ++a) {
+    const std::vector<double> &x = a == 0 ? fs->lon : (a == 1 ? fs->lat : fs->depth);
+    g.lo[a] = x.front(); g.hi[a] = x.back();
+    g.lof[a] = (float)x.front(); g.hif[a] = (float)x.back();
+  }
   const double D = 1852.0 * 60.0;
   for (int a = 0; a < 3; ++a) {
     g.d[a] = fs->inv_d[a] != 0.0 ? 1.0 / fs->inv_d[a] : 0.0;

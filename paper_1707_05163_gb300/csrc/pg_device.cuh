@@ -27,6 +27,8 @@ struct GridArgs {
   float x0f[3], inv_df[3];
   double lon_end;            // lon[0] + 360 (periodic wrap-cell far edge)
   float lon_end_f;
+  double lo[3], hi[3];       // first and last node of each axis (kernel
+  float lof[3], hif[3];      // parameters, so range tests load nothing)
   // uniform axes, cell form: spacing, and metres -> cells factors (lon on a
   // sphere: 1 / (D dlon), still to be divided by cos(lat))
   double d[3];

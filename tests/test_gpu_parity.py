@@ -156,6 +156,45 @@ def test_euler_and_ragged_sizes_fp64(pg):
         assert (g["final"]["time"] == 2 * DAY + 900.0).all()
 
 
+@pytest.mark.parametrize("nt", [1, 3])
+def test_nan_islands_delete_with_nan_status(pg, nt):
+    """NaN nodes (land) make every cell that touches them return NaN; a stage
+    sampling there deletes the particle with PG_NAN and keeps its last valid
+    state.  FP64 matches the oracle bit for bit (flat mesh); the FP32 forms
+    report the same statuses (steady and time-dependent fields)."""
+    import dataclasses
+    base = synth.stommel_gyre(n=61)
+    amp = [1.0, 1.3, 0.7][:nt]
+    data = np.concatenate([base.data * a for a in amp], axis=0).copy()
+    rng = np.random.default_rng(5)
+    for _ in range(25):
+        i, j = rng.integers(3, 58, 2)
+        data[:, :, 0, j:j + 2, i:i + 3] = np.nan
+    times = np.arange(nt) * 5 * DAY if nt > 1 else np.zeros(1)
+    spec = dataclasses.replace(base, data=data, times=times)
+    n = 4000
+    lon = rng.uniform(2e4, 9.8e5, n)
+    lat = rng.uniform(2e4, 9.8e5, n)
+    dt, T = 3600.0, 8 * DAY
+    o = oracle_run(oracle_field(spec), lon, lat, None, 0.0, dt, T)
+    st = o["final"]["status"]
+    assert (st == 3).sum() > 200 and (st == 0).sum() > 1000
+    fs64 = pg.FieldSet.from_spec(spec, storage="f64")
+    g = gpu_run(pg.ParticleSet(fs64, lon, lat, pos="f64"), pg.Kernel("rk4"), T, dt)
+    for k in ("lon", "lat", "status", "step", "time"):
+        np.testing.assert_array_equal(g["final"][k], o["final"][k], err_msg=k)
+    fs32 = pg.FieldSet.from_spec(spec, storage="f32")
+    for pos in ("f32", "cell"):
+        g = gpu_run(pg.ParticleSet(fs32, lon.astype(np.float32), lat.astype(np.float32), pos=pos),
+                    pg.Kernel("rk4"), T, dt)
+        gs = g["final"]["status"]
+        assert set(np.unique(gs)) <= {0, 1, 3}
+        assert np.mean(gs == st) > 0.99, (pos, np.mean(gs == st))
+        alive = (gs == 0) & (st == 0)
+        e = cell_error(g["final"], o["final"], spec, periodic=False)[alive]
+        assert np.mean(e) < 1e-3, (pos, np.mean(e))
+
+
 def test_empty_particle_set(pg):
     fs = pg.FieldSet.from_spec(synth.stommel_gyre(n=11), storage="f64")
     ps = pg.ParticleSet(fs, np.zeros(0), np.zeros(0), pos="f64")
