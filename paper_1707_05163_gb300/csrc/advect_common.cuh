@@ -389,11 +389,16 @@ __device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, St
       // returns a exactly, so the path has no branch on steadiness here.
       const Real b = interp_space<Real, NC>(c.v[1][f], xi, eta, zeta);
       val = fmaf(tau, b, (1.0f - tau) * val);
-      if (!(val == val)) return 3;
     }
     vel[f] = val;
   }
   if constexpr (NF == 2) vel[2] = (Real)0;
+  if constexpr (sizeof(Real) == 4) {
+    // FP32: one NaN test per stage for all components (same outcome as a
+    // test per value: PG_NAN, state untouched), leaving the three
+    // interpolations free of branches
+    if (!(vel[0] == vel[0]) | !(vel[1] == vel[1]) | !(vel[2] == vel[2])) return 3;
+  }
   return 0;
 }
 
