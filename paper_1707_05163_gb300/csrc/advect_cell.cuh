@@ -54,10 +54,13 @@ __device__ __forceinline__ int velocity_cell(const StepArgs &a, Sampler<float, S
   if constexpr (D3) {
     if (!norm_axis(k, z, g.nz, false)) return 2;
   }
-  c.ci = i;
-  c.ci1 = i + 1 == g.nx ? 0 : i + 1;
-  c.cj = j;
-  c.ck = D3 ? k : 0;
+  if (i != c.ci || j != c.cj || (D3 && k != c.ck)) {
+    c.ci = i;
+    c.ci1 = i + 1 == g.nx ? 0 : i + 1;
+    c.cj = j;
+    c.ck = D3 ? k : 0;
+    c.dirty |= 1;
+  }
   const int r = sample_fields(a, c, ck, off, x, y, z, vel);
   if (r) return r;
   if (is_sph<GEO>(g)) {

@@ -140,13 +140,15 @@ struct Sampler {
   Real rx, ry, rz;            // 1 / (hi - lo), FP32 path only
   // cached snapshot interval and the snapshots whose corners are held
   int s0, s1;
-  int gi, gj, gk, gs0, gs1;   // what `v` currently holds (gi = -1: nothing)
+  // what `v` lacks: 1 the cell changed, 2 the snapshot pair moved on by one
+  // (s0 is the old s1), 4 anything else (a new pair, or nothing held yet)
+  int dirty;
   double ta;                  // FP32 path: interval start in unwrapped time
   float span, rspan;          // FP32 path
   Real v[2][NF][NC];
 
   __device__ __forceinline__ void reset() {
-    ci = -1; cj = -1; ck = -1; s0 = -1; s1 = -1; gi = -1;
+    ci = -1; cj = -1; ck = -1; s0 = -1; s1 = -1; dirty = 4;
   }
 };
 
@@ -254,7 +256,6 @@ __device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Sto
 template <typename Real, typename Store, int NF, bool D3, int GEO>
 __device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                        bool steady) {
-  const bool same_cell = c.gi == c.ci && c.gj == c.cj && c.gk == c.ck && c.gi >= 0;
   if (steady) {
     if (!gather_slab(a, c, 0, c.s0)) return false;
     if constexpr (sizeof(Real) == 4) {     // FP32 interpolates both slots
@@ -263,7 +264,7 @@ __device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, N
 #pragma unroll
         for (int q = 0; q < Sampler<Real, Store, NF, D3, GEO>::NC; ++q) c.v[1][f][q] = c.v[0][f][q];
     }
-  } else if (same_cell && c.s0 == c.gs1) {
+  } else if (c.dirty == 2) {
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
@@ -273,7 +274,7 @@ __device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, N
     if (!gather_slab(a, c, 0, c.s0)) return false;
     if (!gather_slab(a, c, 1, c.s1)) return false;
   }
-  c.gi = c.ci; c.gj = c.cj; c.gk = c.ck; c.gs0 = c.s0; c.gs1 = c.s1;
+  c.dirty = 0;
   return true;
 }
 
@@ -341,6 +342,7 @@ __device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, St
         atomicCAS(a.err, 0, (int)DEVERR_TIME_RANGE);
         return -1;
       }
+      if (s0 != c.s0 || s1 != c.s1) c.dirty |= (c.s0 >= 0 && s0 == c.s1) ? 2 : 4;
       c.s0 = s0; c.s1 = s1;
       tau = (tt - ta) / (tb - ta);
     } else {
@@ -354,6 +356,7 @@ __device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, St
           atomicCAS(a.err, 0, (int)DEVERR_TIME_RANGE);
           return -1;
         }
+        if (s0 != c.s0 || s1 != c.s1) c.dirty |= (c.s0 >= 0 && s0 == c.s1) ? 2 : 4;
         c.s0 = s0; c.s1 = s1;
         c.ta = ts - (tt - ta);              // interval start in unwrapped time
         c.span = (float)(tb - ta);
@@ -366,8 +369,7 @@ __device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, St
   } else {
     c.s0 = 0; c.s1 = 0;
   }
-  if (c.gi != c.ci || c.gj != c.cj || c.gk != c.ck || c.gs0 != c.s0 || c.gs1 != c.s1 ||
-      c.gi < 0) {
+  if (c.dirty) {
     if (!gather(a, c, steady)) return -1;
   }
   constexpr int NC = Sampler<Real, Store, NF, D3, GEO>::NC;

@@ -38,6 +38,7 @@ __device__ __forceinline__ bool locate_lon(const GridArgs &g, Sampler<Real, Stor
     return false;
   }
   if (!(c.ci >= 0 && in_cell<Real>(q, c.xlo, c.xhi, c.ci == g.nx - 2 && !is_per<GEO>(g)))) {
+    c.dirty |= 1;
     if (is_per<GEO>(g) && q >= axis_hi(g, 0, p)) {
       c.ci = g.nx - 1; c.ci1 = 0;
       c.xlo = x[g.nx - 1];
@@ -56,12 +57,13 @@ __device__ __forceinline__ bool locate_lon(const GridArgs &g, Sampler<Real, Stor
 
 template <typename Real>
 __device__ __forceinline__ bool locate_axis(const GridArgs &g, int a, int n, int &ci, Real &lo,
-                                            Real &hi, Real &rinv, Real p, Real &xi) {
+                                            Real &hi, Real &rinv, Real p, Real &xi, int &dirty) {
   const Real *x = axis<Real>(g, a);
   if (!(ci >= 0 && in_cell<Real>(p, lo, hi, ci == n - 2))) {
     if (!(p >= x[0] && p <= x[n - 1])) return false;
     const int i = axis_search<Real>(g, a, n, p);
     ci = i; lo = x[i]; hi = x[i + 1];
+    dirty |= 1;
     rinv = (Real)1 / (hi - lo);
   }
   if constexpr (sizeof(Real) == 8) xi = (p - lo) / (hi - lo);
@@ -79,9 +81,9 @@ __device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, 
   const GridArgs &g = a.g;
   Real xi, eta, zeta = (Real)0;
   if (!locate_lon(g, c, lon, xi)) return 1;
-  if (!locate_axis<Real>(g, 1, g.ny, c.cj, c.ylo, c.yhi, c.ry, lat, eta)) return 1;
+  if (!locate_axis<Real>(g, 1, g.ny, c.cj, c.ylo, c.yhi, c.ry, lat, eta, c.dirty)) return 1;
   if constexpr (D3) {
-    if (!locate_axis<Real>(g, 2, g.nz, c.ck, c.zlo, c.zhi, c.rz, dep, zeta)) return 2;
+    if (!locate_axis<Real>(g, 2, g.nz, c.ck, c.zlo, c.zhi, c.rz, dep, zeta, c.dirty)) return 2;
   } else {
     c.ck = 0;
   }
