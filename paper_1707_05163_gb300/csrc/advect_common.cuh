@@ -149,6 +149,7 @@ struct Sampler {
 
   __device__ __forceinline__ void reset() {
     ci = -1; cj = -1; ck = -1; s0 = -1; s1 = -1; dirty = 4;
+    xlo = (Real)1; xhi = (Real)0;   // an empty cell: the first hit test fails
   }
 };
 
@@ -322,6 +323,74 @@ __device__ __forceinline__ float kh_of(const KernArgs &k, float) { return k.kh_f
 __device__ __forceinline__ double w_of(const KernArgs &k, double) { return k.w_sink; }
 __device__ __forceinline__ float w_of(const KernArgs &k, float) { return k.w_sink_f; }
 
+// FP32: bring the snapshot interval of the stage time (step start + off)
+// and the corner cache up to date -- the slow part of a stage, skipped while
+// the stage stays in the cached cell and interval.  The stage time is an
+// FP32 offset inside the cached interval; the FP64 step start is formed only
+// when a stage leaves it.  Returns 0, or -1 for an internal failure recorded
+// in a.err.
+template <typename Store, int NF, bool D3, int GEO>
+__device__ __forceinline__ int refresh32(const StepArgs &a, Sampler<float, Store, NF, D3, GEO> &c,
+                                         Clock &ck, float off) {
+  const bool steady = a.f.nt == 1;
+  if (!steady) {
+    const float d = ck.d + off;
+    if (!(c.s0 >= 0 && d >= 0.f && d <= c.span)) {
+      const double t0 = ck.start();
+      const double ts = t0 + (double)off;
+      double tt, ta, tb;
+      int s0 = c.s0, s1 = c.s1;
+      if (!time_interval(a.f, ts, s0, s1, tt, ta, tb)) {
+        atomicCAS(a.err, 0, (int)DEVERR_TIME_RANGE);
+        return -1;
+      }
+      if (s0 != c.s0 || s1 != c.s1) c.dirty |= (c.s0 >= 0 && s0 == c.s1) ? 2 : 4;
+      c.s0 = s0; c.s1 = s1;
+      c.ta = ts - (tt - ta);              // interval start in unwrapped time
+      c.span = (float)(tb - ta);
+      c.rspan = 1.0f / c.span;
+      ck.d = (float)(t0 - c.ta);
+    }
+  } else {
+    c.s0 = 0; c.s1 = 0;
+  }
+  if (c.dirty) {
+    if (!gather(a, c, steady)) return -1;
+  }
+  return 0;
+}
+
+// FP32 time weight of the stage inside the cached interval (0 for a steady
+// field).
+template <typename Store, int NF, bool D3, int GEO>
+__device__ __forceinline__ float tau32(const StepArgs &a, const Sampler<float, Store, NF, D3, GEO> &c,
+                                       const Clock &ck, float off) {
+  return a.f.nt == 1 ? 0.f : fminf((ck.d + off) * c.rspan, 1.0f);
+}
+
+// FP32 field values from the cached corners: spatial interpolation in both
+// snapshots, then (1 - tau) a + tau b, exact at both ends, so a stage time on
+// a snapshot gives the same value from either neighbouring interval (results
+// do not depend on which interval a thread has cached).  A steady field holds
+// its snapshot in both slots with tau = 0, which returns a exactly, so there
+// is no branch on steadiness.  One NaN test per stage covers all components
+// (same outcome as a test per value: PG_NAN, state untouched) and leaves the
+// interpolations free of branches.  Returns 0 or PG_NAN (3).
+template <typename Store, int NF, bool D3, int GEO>
+__device__ __forceinline__ int interp32(const Sampler<float, Store, NF, D3, GEO> &c, float xi,
+                                        float eta, float zeta, float tau, float (&vel)[3]) {
+  constexpr int NC = Sampler<float, Store, NF, D3, GEO>::NC;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const float va = interp_space<float, NC>(c.v[0][f], xi, eta, zeta);
+    const float vb = interp_space<float, NC>(c.v[1][f], xi, eta, zeta);
+    vel[f] = fmaf(tau, vb, (1.0f - tau) * va);
+  }
+  if constexpr (NF == 2) vel[2] = 0.f;
+  if (!(vel[0] == vel[0]) | !(vel[1] == vel[1]) | !(vel[2] == vel[2])) return 3;
+  return 0;
+}
+
 // Field values (m/s) at a stage, once the cell (c.ci, c.cj, c.ck) and the
 // fractions (xi, eta, zeta) are known: snapshot interval of the stage time
 // (step start + off), corner gather if the cell or interval changed, spatial
@@ -331,10 +400,15 @@ template <typename Real, typename Store, int NF, bool D3, int GEO>
 __device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                              Clock &ck, Real off, Real xi, Real eta, Real zeta,
                                              Real (&vel)[3]) {
-  const bool steady = a.f.nt == 1;
-  Real tau = (Real)0;
-  if (!steady) {
-    if constexpr (sizeof(Real) == 8) {
+  if constexpr (sizeof(Real) == 4) {
+    if (refresh32(a, c, ck, off)) return -1;
+    return interp32(c, xi, eta, zeta, tau32(a, c, ck, off), vel);
+  } else {
+    // FP64: the definition -- interval and a + (b - a) tau for every stage,
+    // and its NaN test per value
+    const bool steady = a.f.nt == 1;
+    Real tau = (Real)0;
+    if (!steady) {
       const double ts = ck.t + (double)off;
       double tt, ta, tb;
       int s0 = c.s0, s1 = c.s1;
@@ -346,62 +420,25 @@ __device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, St
       c.s0 = s0; c.s1 = s1;
       tau = (tt - ta) / (tb - ta);
     } else {
-      float d = ck.d + (float)off;
-      if (!(c.s0 >= 0 && d >= 0.f && d <= c.span)) {
-        const double t0 = ck.start();
-        const double ts = t0 + (double)off;
-        double tt, ta, tb;
-        int s0 = c.s0, s1 = c.s1;
-        if (!time_interval(a.f, ts, s0, s1, tt, ta, tb)) {
-          atomicCAS(a.err, 0, (int)DEVERR_TIME_RANGE);
-          return -1;
-        }
-        if (s0 != c.s0 || s1 != c.s1) c.dirty |= (c.s0 >= 0 && s0 == c.s1) ? 2 : 4;
-        c.s0 = s0; c.s1 = s1;
-        c.ta = ts - (tt - ta);              // interval start in unwrapped time
-        c.span = (float)(tb - ta);
-        c.rspan = 1.0f / c.span;
-        d = (float)(tt - ta);
-        ck.d = (float)(t0 - c.ta);
-      }
-      tau = fminf(d * c.rspan, 1.0f);
+      c.s0 = 0; c.s1 = 0;
     }
-  } else {
-    c.s0 = 0; c.s1 = 0;
-  }
-  if (c.dirty) {
-    if (!gather(a, c, steady)) return -1;
-  }
-  constexpr int NC = Sampler<Real, Store, NF, D3, GEO>::NC;
+    if (c.dirty) {
+      if (!gather(a, c, steady)) return -1;
+    }
+    constexpr int NC = Sampler<Real, Store, NF, D3, GEO>::NC;
 #pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    Real val = interp_space<Real, NC>(c.v[0][f], xi, eta, zeta);
-    if constexpr (sizeof(Real) == 8) {
-      // the definition's a + (b - a) tau, and its NaN test per value
+    for (int f = 0; f < NF; ++f) {
+      Real val = interp_space<Real, NC>(c.v[0][f], xi, eta, zeta);
       if (!steady) {
         const Real b = interp_space<Real, NC>(c.v[1][f], xi, eta, zeta);
         val = val + (b - val) * tau;
       }
       if (!(val == val)) return 3;
-    } else {
-      // (1 - tau) a + tau b, exact at both ends, so a stage time on a
-      // snapshot gives the same value from either neighbouring interval
-      // (results do not depend on which interval a thread has cached).  A
-      // steady field holds its snapshot in both slots with tau = 0, which
-      // returns a exactly, so the path has no branch on steadiness here.
-      const Real b = interp_space<Real, NC>(c.v[1][f], xi, eta, zeta);
-      val = fmaf(tau, b, (1.0f - tau) * val);
+      vel[f] = val;
     }
-    vel[f] = val;
+    if constexpr (NF == 2) vel[2] = (Real)0;
+    return 0;
   }
-  if constexpr (NF == 2) vel[2] = (Real)0;
-  if constexpr (sizeof(Real) == 4) {
-    // FP32: one NaN test per stage for all components (same outcome as a
-    // test per value: PG_NAN, state untouched), leaving the three
-    // interpolations free of branches
-    if (!(vel[0] == vel[0]) | !(vel[1] == vel[1]) | !(vel[2] == vel[2])) return 3;
-  }
-  return 0;
 }
 
 }  // namespace pg

@@ -79,6 +79,40 @@ __device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, 
                                         Clock &ck, Real off, Real lon, Real lat, Real dep,
                                         Real (&vel)[3]) {
   const GridArgs &g = a.g;
+  if constexpr (sizeof(Real) == 4) {
+    // FP32: one predicate tests the cached cell on every axis and the cached
+    // snapshot interval; only a miss runs the locate / interval / gather
+    // path, so the common stage is one block without branches.
+    const float x0 = axis_lo(g, 0, lon);
+    float q = lon;
+    if (is_per<GEO>(g)) q = lon < x0 ? lon + 360.0f : (lon >= x0 + 360.0f ? lon - 360.0f : lon);
+    const float d = ck.d + off;
+    bool hit = (q >= c.xlo) & (q <= c.xhi) & (lat >= c.ylo) & (lat <= c.yhi);
+    if constexpr (D3) hit = hit & (dep >= c.zlo) & (dep <= c.zhi);
+    hit = hit & ((a.f.nt == 1) | ((c.s0 >= 0) & (d >= 0.f) & (d <= c.span)));
+    float xi, eta, zeta = 0.f;
+    if (!hit) {
+      if (!locate_lon(g, c, lon, xi)) return 1;
+      if (!locate_axis<float>(g, 1, g.ny, c.cj, c.ylo, c.yhi, c.ry, lat, eta, c.dirty)) return 1;
+      if constexpr (D3) {
+        if (!locate_axis<float>(g, 2, g.nz, c.ck, c.zlo, c.zhi, c.rz, dep, zeta, c.dirty)) return 2;
+      } else {
+        c.ck = 0;
+      }
+      if (refresh32(a, c, ck, off)) return -1;
+      if (is_per<GEO>(g)) q = wrap_lon(lon, x0);
+    }
+    xi = (q - c.xlo) * c.rx;
+    eta = (lat - c.ylo) * c.ry;
+    if constexpr (D3) zeta = (dep - c.zlo) * c.rz;
+    const int r = interp32(c, xi, eta, zeta, tau32(a, c, ck, off), vel);
+    if (r) return r;
+    if (is_sph<GEO>(g)) {
+      vel[0] = lon_rate(vel[0], lat, a.k);
+      vel[1] = lat_rate(vel[1], a.k);
+    }
+    return 0;
+  }
   Real xi, eta, zeta = (Real)0;
   if (!locate_lon(g, c, lon, xi)) return 1;
   if (!locate_axis<Real>(g, 1, g.ny, c.cj, c.ylo, c.yhi, c.ry, lat, eta, c.dirty)) return 1;
