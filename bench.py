@@ -47,8 +47,8 @@ def parse():
     ap.add_argument("--snapshots", type=int, default=30,
                     help="daily snapshots in the periodic field (30 = the workload)")
     ap.add_argument("--block", type=int, default=128)
-    ap.add_argument("--resort-steps", type=int, default=96)
-    ap.add_argument("--chunk-steps", type=int, default=48)
+    ap.add_argument("--resort-steps", type=int, default=288)
+    ap.add_argument("--chunk-steps", type=int, default=288)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -93,16 +93,17 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch():
-    """DRAM bytes per launch of the advection kernel from a committed ncu
-    capture, if it was taken on the current kernel source; else None."""
+def traffic_per_launch(particle_steps_per_launch):
+    """DRAM bytes per launch of the advection kernel: the per-particle-step
+    DRAM bytes of a committed ncu capture (taken on the current kernel source,
+    else None) times the particle-steps of one launch."""
     p = os.path.join(ROOT, "profiles", "advect_f32_3d_traffic.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p))
         if d.get("kernel_hash") == kernel_hash():
-            return float(d["dram_bytes_per_launch"])
+            return float(d["dram_bytes_per_particle_step"]) * particle_steps_per_launch
     except Exception:
         pass
     return None
@@ -307,7 +308,7 @@ def main():
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = ALGO_FLOPS_PER_STEP * steps_per_launch / avg_launch_s / 1e12
     gather_gbs = ALGO_BYTES_PER_STEP * steps_per_launch / avg_launch_s / 1e9
-    traffic = traffic_per_launch()
+    traffic = traffic_per_launch(steps_per_launch)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
@@ -322,7 +323,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
-                     "kernel": "advect_plain_kernel<float,float,3,true>",
+                     "kernel": "advect_plain_kernel<float, float, 3, true, GEO_SPH_PER>",
                      "algorithmic_flops_per_particle_step": ALGO_FLOPS_PER_STEP,
                      "avg_launch_ms": avg_launch_s * 1e3, "launches": kern_launches,
                      "gather_view": {"algorithmic_bytes_per_particle_step": ALGO_BYTES_PER_STEP,
