@@ -75,7 +75,21 @@ __device__ __forceinline__ double cos_deg(double lat) {
   const double deg2rad = 3.14159265358979323846 / 180.0;
   return cos(lat * deg2rad);
 }
-__device__ __forceinline__ float cos_deg(float lat) { return cospif(lat * (1.0f / 180.0f)); }
+// FP32: the Taylor series of cos x to the x^12 term, x = lat in radians,
+// evaluated by Horner's rule in x^2.  On |x| <= pi/2 the remainder is below
+// x^14 / 14! < 7e-9; the rounding of x itself dominates (a relative error of
+// 7e-7 at 80 degrees, as for any FP32 argument), and there is no range
+// reduction or branch.
+__device__ __forceinline__ float cos_deg(float lat) {
+  const float x = lat * 0.017453292519943295f;
+  const float x2 = x * x;
+  float p = fmaf(x2, 1.0f / 479001600.0f, -1.0f / 3628800.0f);
+  p = fmaf(x2, p, 1.0f / 40320.0f);
+  p = fmaf(x2, p, -1.0f / 720.0f);
+  p = fmaf(x2, p, 1.0f / 24.0f);
+  p = fmaf(x2, p, -0.5f);
+  return fmaf(x2, p, 1.0f);
+}
 
 // u (m/s) -> degrees/s of longitude at latitude lat; v (m/s) -> degrees/s.
 __device__ __forceinline__ double lon_rate(double u, double lat, const KernArgs &k) {
@@ -279,8 +293,9 @@ __device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, N
   return true;
 }
 
-// Bilinear weights applied as (w00 f00 + w10 f10) + (w11 f11 + w01 f01);
-// trilinear is linear in zeta between the two levels.
+// FP64 spatial interpolation in the definition's order: bilinear weights
+// applied as (w00 f00 + w10 f10) + (w11 f11 + w01 f01); trilinear is linear in
+// zeta between the two levels.
 template <typename Real, int NC>
 __device__ __forceinline__ Real interp_space(const Real (&v)[NC], Real xi, Real eta, Real zeta) {
   const Real w00 = ((Real)1 - xi) * ((Real)1 - eta);
@@ -368,8 +383,36 @@ __device__ __forceinline__ float tau32(const StepArgs &a, const Sampler<float, S
   return a.f.nt == 1 ? 0.f : fminf((ck.d + off) * c.rspan, 1.0f);
 }
 
+// FP32 spatial interpolation as one weighted sum over the corners, the
+// weights formed once per stage (bilinear, or trilinear as the bilinear
+// weights times 1 - zeta and zeta).  The sum runs in corner order (i, j),
+// (i+1, j), (i, j+1), (i+1, j+1)[, the same on level k+1] as one chain of
+// fused multiply-adds; on a cell face the weights of the far corners are
+// exactly 0 and the remaining terms come in the same order from either
+// neighbouring cell, so the two cells give the same value there.
+template <int NC>
+__device__ __forceinline__ void corner_weights(float xi, float eta, float zeta, float (&w)[NC]) {
+  const float x0 = 1.f - xi, y0 = 1.f - eta;
+  const float w00 = x0 * y0, w10 = xi * y0, w01 = x0 * eta, w11 = xi * eta;
+  if constexpr (NC == 4) {
+    w[0] = w00; w[1] = w10; w[2] = w01; w[3] = w11;
+  } else {
+    const float z0 = 1.f - zeta;
+    w[0] = w00 * z0; w[1] = w10 * z0; w[2] = w01 * z0; w[3] = w11 * z0;
+    w[4] = w00 * zeta; w[5] = w10 * zeta; w[6] = w01 * zeta; w[7] = w11 * zeta;
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ float weighted_sum(const float (&v)[NC], const float (&w)[NC]) {
+  float acc = w[0] * v[0];
+#pragma unroll
+  for (int q = 1; q < NC; ++q) acc = fmaf(w[q], v[q], acc);
+  return acc;
+}
+
 // FP32 field values from the cached corners: spatial interpolation in both
-// snapshots, then (1 - tau) a + tau b, exact at both ends, so a stage time on
+// snapshots (weighted_sum), then (1 - tau) a + tau b, exact at both ends, so a stage time on
 // a snapshot gives the same value from either neighbouring interval (results
 // do not depend on which interval a thread has cached).  A steady field holds
 // its snapshot in both slots with tau = 0, which returns a exactly, so there
@@ -380,10 +423,12 @@ template <typename Store, int NF, bool D3, int GEO>
 __device__ __forceinline__ int interp32(const Sampler<float, Store, NF, D3, GEO> &c, float xi,
                                         float eta, float zeta, float tau, float (&vel)[3]) {
   constexpr int NC = Sampler<float, Store, NF, D3, GEO>::NC;
+  float w[NC];
+  corner_weights<NC>(xi, eta, zeta, w);
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    const float va = interp_space<float, NC>(c.v[0][f], xi, eta, zeta);
-    const float vb = interp_space<float, NC>(c.v[1][f], xi, eta, zeta);
+    const float va = weighted_sum<NC>(c.v[0][f], w);
+    const float vb = weighted_sum<NC>(c.v[1][f], w);
     vel[f] = fmaf(tau, vb, (1.0f - tau) * va);
   }
   if constexpr (NF == 2) vel[2] = 0.f;

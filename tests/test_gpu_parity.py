@@ -259,6 +259,28 @@ def test_fp32_each_mesh_geometry(pg, geo):
     assert g["steps"] == o["steps"]
 
 
+@pytest.mark.parametrize("pos", ["f32", "cell"])
+def test_fp32_metres_to_degrees_on_the_sphere(pg, pos):
+    """Uniform 1 m/s eastward flow on the sphere (Sect. 4.2.2): one RK4 step of
+    one day moves a particle by u dt / (1852 * 60 * cos(lat)) degrees of
+    longitude exactly (every stage sees the same velocity), so the FP32 step
+    pins the FP32 cos(lat) and the metres-to-degrees conversion to a few ulps
+    from the equator to 80 degrees."""
+    spec = synth.zonal_flow_sphere()
+    lat = np.linspace(-79.75, 79.75, 320)
+    lon = np.full(lat.shape, 0.5)
+    fs = pg.FieldSet.from_spec(spec, storage="f32")
+    ps = pg.ParticleSet(fs, lon.astype(np.float32), lat.astype(np.float32), pos=pos)
+    ps.execute(pg.Kernel("rk4"), DAY, DAY)
+    g = ps.get()
+    lat32 = lat.astype(np.float32).astype(np.float64)
+    want = 0.5 + DAY / (1852.0 * 60.0 * np.cos(np.deg2rad(lat32)))
+    rel = np.abs(g["lon"] - want) / (want - 0.5)
+    assert (g["status"] == 0).all()
+    np.testing.assert_array_equal(g["lat"], lat32)
+    assert rel.max() < 3e-6, rel.max()
+
+
 @pytest.mark.parametrize("storage,kind", [("f16", 0), ("bf16", 1)])
 def test_quantised_storage_scales_and_trajectories(pg, storage, kind):
     gf, spec = _small_global(nz=1, res=1.0)
