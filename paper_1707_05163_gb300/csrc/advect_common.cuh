@@ -418,8 +418,9 @@ __device__ __forceinline__ float weighted_sum(const float (&v)[NC], const float 
 // its snapshot in both slots with tau = 0, which returns a exactly, so there
 // is no branch on steadiness.  One NaN test per stage covers all components
 // (same outcome as a test per value: PG_NAN, state untouched) and leaves the
-// interpolations free of branches.  Returns 0 or PG_NAN (3).
-template <typename Store, int NF, bool D3, int GEO>
+// interpolations free of branches; CHECK = false leaves the test to the
+// caller.  Returns 0 or PG_NAN (3).
+template <typename Store, int NF, bool D3, int GEO, bool CHECK = true>
 __device__ __forceinline__ int interp32(const Sampler<float, Store, NF, D3, GEO> &c, float xi,
                                         float eta, float zeta, float tau, float (&vel)[3]) {
   constexpr int NC = Sampler<float, Store, NF, D3, GEO>::NC;
@@ -432,7 +433,7 @@ __device__ __forceinline__ int interp32(const Sampler<float, Store, NF, D3, GEO>
     vel[f] = fmaf(tau, vb, (1.0f - tau) * va);
   }
   if constexpr (NF == 2) vel[2] = 0.f;
-  if (!(vel[0] == vel[0]) | !(vel[1] == vel[1]) | !(vel[2] == vel[2])) return 3;
+  if (CHECK && (!(vel[0] == vel[0]) | !(vel[1] == vel[1]) | !(vel[2] == vel[2]))) return 3;
   return 0;
 }
 

@@ -92,10 +92,18 @@ __device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, 
     hit = hit & ((a.f.nt == 1) | ((c.s0 >= 0) & (d >= 0.f) & (d <= c.span)));
     float xi, eta, zeta = 0.f;
     if (!hit) {
-      if (!locate_lon(g, c, lon, xi)) return 1;
-      if (!locate_axis<float>(g, 1, g.ny, c.cj, c.ylo, c.yhi, c.ry, lat, eta, c.dirty)) return 1;
+      // The stage velocities are not tested for NaN: a NaN velocity makes
+      // the next stage position (or the step's result) NaN, which fails its
+      // range test, and a failed test on a NaN position reports PG_NAN --
+      // the status and the kept state of the definition's per-value test.
+      // (Infinite velocities give infinite, not NaN, positions.)
+      const int nan = (!(lon == lon) | !(lat == lat) | !(dep == dep)) ? 3 : 0;
+      if (!locate_lon(g, c, lon, xi)) return nan ? nan : 1;
+      if (!locate_axis<float>(g, 1, g.ny, c.cj, c.ylo, c.yhi, c.ry, lat, eta, c.dirty))
+        return nan ? nan : 1;
       if constexpr (D3) {
-        if (!locate_axis<float>(g, 2, g.nz, c.ck, c.zlo, c.zhi, c.rz, dep, zeta, c.dirty)) return 2;
+        if (!locate_axis<float>(g, 2, g.nz, c.ck, c.zlo, c.zhi, c.rz, dep, zeta, c.dirty))
+          return nan ? nan : 2;
       } else {
         c.ck = 0;
       }
@@ -105,7 +113,7 @@ __device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, 
     xi = (q - c.xlo) * c.rx;
     eta = (lat - c.ylo) * c.ry;
     if constexpr (D3) zeta = (dep - c.zlo) * c.rz;
-    const int r = interp32(c, xi, eta, zeta, tau32(a, c, ck, off), vel);
+    const int r = interp32<Store, NF, D3, GEO, false>(c, xi, eta, zeta, tau32(a, c, ck, off), vel);
     if (r) return r;
     if (is_sph<GEO>(g)) {
       vel[0] = lon_rate(vel[0], lat, a.k);
@@ -142,6 +150,22 @@ __device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, 
   const Real half = (Real)0.5 * hr;
   const int nst = a.k.scheme == 0 ? 1 : 4;
   int r;
+  if constexpr (sizeof(Real) == 4) {
+    // FP32: the same sums without branches on the stage: offsets c_s h with
+    // c = (0, 1/2, 1/2, 1), weights (1, 2, 2, 1); 2 k and c_s h are exact
+    acc[0] = 0.f; acc[1] = 0.f; acc[2] = 0.f;
+#pragma unroll 1
+    for (int s = 0; s < nst; ++s) {
+      const float off = (s == 0 ? 0.f : (s == 3 ? 1.f : 0.5f)) * hr;
+      const float px = fmaf(kc[0], off, lon), py = fmaf(kc[1], off, lat);
+      const float pz = fmaf(kc[2], off, dep);
+      if ((r = velocity(a, c, ck, off, px, py, pz, kc))) return r;
+      const float wg = (s == 1 || s == 2) ? 2.f : 1.f;
+      acc[0] = fmaf(wg, kc[0], acc[0]);
+      acc[1] = fmaf(wg, kc[1], acc[1]);
+      acc[2] = fmaf(wg, kc[2], acc[2]);
+    }
+  } else
 #pragma unroll 1
   for (int s = 0; s < nst; ++s) {
     const Real off = s == 0 ? (Real)0 : (s == 3 ? hr : half);
@@ -186,7 +210,13 @@ __device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, 
   }
   if (a.k.beh & 2u) ndep = ndep + w_of(a.k, hr) * hr;
   if (is_per<GEO>(a.g)) nlon = wrap_lon(nlon, axis_lo(a.g, 0, nlon));
-  if ((r = out_of_domain<Real, GEO>(a.g, nlon, nlat, ndep, D3))) return r;
+  if ((r = out_of_domain<Real, GEO>(a.g, nlon, nlat, ndep, D3))) {
+    // FP32: a NaN result comes from a NaN stage velocity (see velocity)
+    if constexpr (sizeof(Real) == 4) {
+      if (!(nlon == nlon) | !(nlat == nlat) | !(ndep == ndep)) return 3;
+    }
+    return r;
+  }
   lon = nlon; lat = nlat; dep = ndep;
   return 0;
 }
