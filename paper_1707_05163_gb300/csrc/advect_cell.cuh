@@ -56,7 +56,6 @@ __device__ __forceinline__ int velocity_cell(const StepArgs &a, Sampler<float, S
   }
   if (i != c.ci || j != c.cj || (D3 && k != c.ck)) {
     c.ci = i;
-    c.ci1 = i + 1 == g.nx ? 0 : i + 1;
     c.cj = j;
     c.ck = D3 ? k : 0;
     c.dirty |= 1;
@@ -77,7 +76,7 @@ __device__ __forceinline__ int velocity_cell(const StepArgs &a, Sampler<float, S
 // One step of Eq. 1 in cell units; the state is replaced only on success.
 template <typename Store, int NF, bool D3, int GEO>
 __device__ __forceinline__ int step_cell(const StepArgs &a, Sampler<float, Store, NF, D3, GEO> &c,
-                                         Clock &ck, CellState &s, float h, uint64_t id,
+                                         Clock &ck, CellState &s, float h, const uint64_t *idp,
                                          uint32_t stp) {
   const GridArgs &g = a.g;
   float kc[3] = {0.f, 0.f, 0.f};
@@ -104,7 +103,7 @@ __device__ __forceinline__ int step_cell(const StepArgs &a, Sampler<float, Store
   n.z = D3 ? s.z + acc[2] * w : 0.f;
   if (a.k.beh & 1u) {
     float n1, n2;
-    normal_pair(a.k.seed, id, stp, n1, n2);
+    normal_pair(a.k.seed, *idp, stp, n1, n2);
     const float sigma = sqrtf(2.f * a.k.kh_f * fabsf(h));
     float dx = sigma * n1 * g.inv_m[0];
     if (is_sph<GEO>(g)) dx = __fdividef(dx, cos_deg(g.x0f[1] + ((float)n.j + n.y) * g.df[1]));
@@ -131,7 +130,7 @@ __global__ void __launch_bounds__(256, 2) advect_cell_kernel(StepArgs a) {
     if (D3) { s.k = a.p.ck[p]; s.z = a.p.fz[p]; } else { s.k = 0; s.z = 0.f; }
     double t = a.p.time[p];
     uint32_t stp = a.p.step[p];
-    const uint64_t id = a.p.id[p];
+    const uint64_t *idp = a.p.id + p;   // read by the Brownian step only
     uint8_t st = 0;
     Sampler<float, Store, NF, D3, GEO> c;
     c.reset();
@@ -151,7 +150,7 @@ __global__ void __launch_bounds__(256, 2) advect_cell_kernel(StepArgs a) {
     for (; k < n; ++k) {
       ck.k = k;
       const float h = (k == n - 1) ? hlf : hf;
-      const int r = step_cell(a, c, ck, s, h, id, stp);
+      const int r = step_cell(a, c, ck, s, h, idp, stp);
       if (r > 0) { st = (uint8_t)r; break; }
       if (r < 0) break;
       ++stp;

@@ -149,11 +149,11 @@ template <typename Real, typename Store, int NF, bool D3, int GEO = GEO_ANY>
 struct Sampler {
   static constexpr int NC = D3 ? 8 : 4;
   // cached cell (ci = -1: none) and its bounds
-  int ci, ci1, cj, ck;
+  int ci, cj, ck;
   Real xlo, xhi, ylo, yhi, zlo, zhi;
   Real rx, ry, rz;            // 1 / (hi - lo), FP32 path only
   // cached snapshot interval and the snapshots whose corners are held
-  int s0, s1;
+  int s0;                     // first snapshot of the cached pair (second: snap_next)
   // what `v` lacks: 1 the cell changed, 2 the snapshot pair moved on by one
   // (s0 is the old s1), 4 anything else (a new pair, or nothing held yet)
   int dirty;
@@ -162,7 +162,7 @@ struct Sampler {
   Real v[2][NF][NC];
 
   __device__ __forceinline__ void reset() {
-    ci = -1; cj = -1; ck = -1; s0 = -1; s1 = -1; dirty = 4;
+    ci = -1; cj = -1; ck = -1; s0 = -1; dirty = 4;
     xlo = (Real)1; xhi = (Real)0;   // an empty cell: the first hit test fails
   }
 };
@@ -234,6 +234,13 @@ __device__ __forceinline__ bool time_interval(const FieldArgs &f, double t, int 
   return true;
 }
 
+// Second snapshot of the pair that starts at s0: s0 + 1, or the first
+// snapshot after the last one (periodic fields; a steady field's pair is
+// (0, 0)).  These are the only pairs time_interval returns.
+__device__ __forceinline__ int snap_next(const FieldArgs &f, int s0) {
+  return s0 + 1 < f.nt ? s0 + 1 : 0;
+}
+
 template <typename Real, typename Store, int NF, bool D3, int GEO>
 __device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                             int sl, int s) {
@@ -243,6 +250,7 @@ __device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Sto
     atomicCAS(a.err, 0, (int)DEVERR_SLAB_MISSING);
     return false;
   }
+  const int ci1 = c.ci + 1 == g.nx ? 0 : c.ci + 1;   // the periodic wrap cell joins nx-1 to 0
   float sc[3] = {1.f, 1.f, 1.f};
   if (a.f.scales != nullptr) {
 #pragma unroll
@@ -256,7 +264,7 @@ __device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Sto
 #pragma unroll
       for (int ii = 0; ii < 2; ++ii) {
         Real vv[NF];
-        load_node<Real, NF>(base, row + (size_t)(ii ? c.ci1 : c.ci), sc, vv);
+        load_node<Real, NF>(base, row + (size_t)(ii ? ci1 : c.ci), sc, vv);
 #pragma unroll
         for (int f = 0; f < NF; ++f) c.v[sl][f][kk * 4 + jj * 2 + ii] = vv[f];
       }
@@ -284,10 +292,10 @@ __device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, N
     for (int f = 0; f < NF; ++f)
 #pragma unroll
       for (int q = 0; q < Sampler<Real, Store, NF, D3, GEO>::NC; ++q) c.v[0][f][q] = c.v[1][f][q];
-    if (!gather_slab(a, c, 1, c.s1)) return false;
+    if (!gather_slab(a, c, 1, snap_next(a.f, c.s0))) return false;
   } else {
     if (!gather_slab(a, c, 0, c.s0)) return false;
-    if (!gather_slab(a, c, 1, c.s1)) return false;
+    if (!gather_slab(a, c, 1, snap_next(a.f, c.s0))) return false;
   }
   c.dirty = 0;
   return true;
@@ -354,20 +362,20 @@ __device__ __forceinline__ int refresh32(const StepArgs &a, Sampler<float, Store
       const double t0 = ck.start();
       const double ts = t0 + (double)off;
       double tt, ta, tb;
-      int s0 = c.s0, s1 = c.s1;
+      int s0 = c.s0, s1 = snap_next(a.f, c.s0);
       if (!time_interval(a.f, ts, s0, s1, tt, ta, tb)) {
         atomicCAS(a.err, 0, (int)DEVERR_TIME_RANGE);
         return -1;
       }
-      if (s0 != c.s0 || s1 != c.s1) c.dirty |= (c.s0 >= 0 && s0 == c.s1) ? 2 : 4;
-      c.s0 = s0; c.s1 = s1;
+      if (s0 != c.s0) c.dirty |= (c.s0 >= 0 && s0 == snap_next(a.f, c.s0)) ? 2 : 4;
+      c.s0 = s0;
       c.ta = ts - (tt - ta);              // interval start in unwrapped time
       c.span = (float)(tb - ta);
       c.rspan = 1.0f / c.span;
       ck.d = (float)(t0 - c.ta);
     }
   } else {
-    c.s0 = 0; c.s1 = 0;
+    c.s0 = 0;
   }
   if (c.dirty) {
     if (!gather(a, c, steady)) return -1;
@@ -457,16 +465,16 @@ __device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, St
     if (!steady) {
       const double ts = ck.t + (double)off;
       double tt, ta, tb;
-      int s0 = c.s0, s1 = c.s1;
+      int s0 = c.s0, s1 = snap_next(a.f, c.s0);
       if (!time_interval(a.f, ts, s0, s1, tt, ta, tb)) {
         atomicCAS(a.err, 0, (int)DEVERR_TIME_RANGE);
         return -1;
       }
-      if (s0 != c.s0 || s1 != c.s1) c.dirty |= (c.s0 >= 0 && s0 == c.s1) ? 2 : 4;
-      c.s0 = s0; c.s1 = s1;
+      if (s0 != c.s0) c.dirty |= (c.s0 >= 0 && s0 == snap_next(a.f, c.s0)) ? 2 : 4;
+      c.s0 = s0;
       tau = (tt - ta) / (tb - ta);
     } else {
-      c.s0 = 0; c.s1 = 0;
+      c.s0 = 0;
     }
     if (c.dirty) {
       if (!gather(a, c, steady)) return -1;

@@ -40,12 +40,12 @@ __device__ __forceinline__ bool locate_lon(const GridArgs &g, Sampler<Real, Stor
   if (!(c.ci >= 0 && in_cell<Real>(q, c.xlo, c.xhi, c.ci == g.nx - 2 && !is_per<GEO>(g)))) {
     c.dirty |= 1;
     if (is_per<GEO>(g) && q >= axis_hi(g, 0, p)) {
-      c.ci = g.nx - 1; c.ci1 = 0;
+      c.ci = g.nx - 1;
       c.xlo = x[g.nx - 1];
       c.xhi = lon_end(g, p);
     } else {
       const int i = axis_search<Real>(g, 0, g.nx, q);
-      c.ci = i; c.ci1 = i + 1;
+      c.ci = i;
       c.xlo = x[i]; c.xhi = x[i + 1];
     }
     c.rx = (Real)1 / (c.xhi - c.xlo);
@@ -144,7 +144,7 @@ __device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, 
 template <typename Real, typename Store, int NF, bool D3, int GEO>
 __device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                         Clock &ck, Real &lon, Real &lat, Real &dep, Real hr,
-                                        uint64_t id, uint32_t stp) {
+                                        const uint64_t *idp, uint32_t stp) {
   Real kc[3] = {(Real)0, (Real)0, (Real)0};
   Real acc[3];
   const Real half = (Real)0.5 * hr;
@@ -198,7 +198,7 @@ __device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, 
   }
   if (a.k.beh & 1u) {
     Real n1, n2;
-    normal_pair(a.k.seed, id, stp, n1, n2);
+    normal_pair(a.k.seed, *idp, stp, n1, n2);
     const Real sigma = pg_sqrt((Real)2 * kh_of(a.k, hr) * pg_fabs(hr));
     Real dx = sigma * n1, dy = sigma * n2;
     if (is_sph<GEO>(a.g)) {
@@ -234,7 +234,7 @@ __device__ __forceinline__ unsigned long long advance_particle(const StepArgs &a
     Real lon = X[p], lat = Y[p], dep = Z[p];
     double t = a.p.time[p];
     uint32_t stp = a.p.step[p];
-    const uint64_t id = a.p.id[p];
+    const uint64_t *idp = a.p.id + p;   // read by the Brownian step only
     uint8_t st = 0;
     Sampler<Real, Store, NF, D3, GEO> c;
     c.reset();
@@ -247,7 +247,7 @@ __device__ __forceinline__ unsigned long long advance_particle(const StepArgs &a
         double h = a.dt;
         if (sgn * (a.t_end - t) < sgn * h) h = a.t_end - t;
         ck.t = t;
-        const int r = step_one(a, c, ck, lon, lat, dep, (Real)h, id, stp);
+        const int r = step_one(a, c, ck, lon, lat, dep, (Real)h, idp, stp);
         if (r > 0) { st = (uint8_t)r; break; }
         if (r < 0) break;
         t = t + h;
@@ -270,7 +270,7 @@ __device__ __forceinline__ unsigned long long advance_particle(const StepArgs &a
       for (; k < n; ++k) {
         ck.k = k;
         const float h = (k == n - 1) ? hlf : hf;
-        const int r = step_one(a, c, ck, lon, lat, dep, (Real)h, id, stp);
+        const int r = step_one(a, c, ck, lon, lat, dep, (Real)h, idp, stp);
         if (r > 0) { st = (uint8_t)r; break; }
         if (r < 0) break;
         ++stp;
