@@ -163,7 +163,10 @@ struct Sampler {
 
   __device__ __forceinline__ void reset() {
     ci = -1; cj = -1; ck = -1; s0 = -1; dirty = 4;
-    xlo = (Real)1; xhi = (Real)0;   // an empty cell: the first hit test fails
+    // empty cells on every axis: the first hit test of each axis fails
+    xlo = (Real)1; xhi = (Real)0;
+    ylo = (Real)1; yhi = (Real)0;
+    zlo = (Real)1; zhi = (Real)0;
   }
 };
 
@@ -248,6 +251,14 @@ __device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Sto
   const Store *base = reinterpret_cast<const Store *>(a.f.tab[s]);
   if (base == nullptr) {
     atomicCAS(a.err, 0, (int)DEVERR_SLAB_MISSING);
+    return false;
+  }
+  // the cached cell must be a cell of the grid (the periodic wrap cell is
+  // nx-1, joining node nx-1 to node 0); anything else is an internal error
+  // recorded in a.err, never a read outside the slab
+  if (!((unsigned)c.ci < (unsigned)g.nx && (unsigned)c.cj <= (unsigned)(g.ny - 2) &&
+        (!D3 || (unsigned)c.ck <= (unsigned)(g.nz - 2)) && (D3 || c.ck == 0))) {
+    atomicCAS(a.err, 0, (int)DEVERR_CELL_INDEX);
     return false;
   }
   const int ci1 = c.ci + 1 == g.nx ? 0 : c.ci + 1;   // the periodic wrap cell joins nx-1 to 0

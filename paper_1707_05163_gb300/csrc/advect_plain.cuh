@@ -71,6 +71,38 @@ __device__ __forceinline__ bool locate_axis(const GridArgs &g, int a, int n, int
   return true;
 }
 
+// FP32 slow path: locate p, known to lie outside the cached cell [lo, hi] of
+// index ci on axis a (n nodes), and refresh the cell.  A move to a neighbour
+// cell costs one load (the far node of the neighbour; the shared node is the
+// old lo or hi); anything else searches the axis.  The cell found is the
+// largest i <= n-2 with x[i] <= p, as a fresh search gives.
+__device__ __forceinline__ void relocate32(const GridArgs &g, int a, int n, float p, int &ci,
+                                           float &lo, float &hi, float &rinv) {
+  const float *x = axis<float>(g, a);
+  int i = -1;
+  float nlo = 0.f, nhi = 0.f;
+  if (ci >= 0 && ci <= n - 2) {
+    if (p < lo) {
+      if (ci >= 1) {
+        const float xm = x[ci - 1];
+        if (xm <= p) { i = ci - 1; nlo = xm; nhi = lo; }
+      }
+    } else if (ci + 1 <= n - 2) {   // p > hi
+      const float x2 = x[ci + 2];
+      if (p < x2 || (ci + 1 == n - 2 && p == x2)) { i = ci + 1; nlo = hi; nhi = x2; }
+    }
+  }
+  if (i < 0) {
+    i = axis_search<float>(g, a, n, p);
+    nlo = x[i];
+    nhi = x[i + 1];
+  }
+  ci = i;
+  lo = nlo;
+  hi = nhi;
+  rinv = __frcp_rn(nhi - nlo);   // correctly rounded, as 1.0f / (hi - lo)
+}
+
 // Velocity in position units per second at a stage (stage time = step start
 // + off).  Returns 0 or a particle status (PG_OOB_*, PG_NAN); -1 for an
 // internal failure already recorded in a.err.
@@ -97,18 +129,41 @@ __device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, 
       // range test, and a failed test on a NaN position reports PG_NAN --
       // the status and the kept state of the definition's per-value test.
       // (Infinite velocities give infinite, not NaN, positions.)
+      // each axis whose cached cell fails is located again (the Sampler
+      // starts with empty cells on every axis, so all fail the first time)
       const int nan = (!(lon == lon) | !(lat == lat) | !(dep == dep)) ? 3 : 0;
-      if (!locate_lon(g, c, lon, xi)) return nan ? nan : 1;
-      if (!locate_axis<float>(g, 1, g.ny, c.cj, c.ylo, c.yhi, c.ry, lat, eta, c.dirty))
-        return nan ? nan : 1;
+      if (!((q >= c.xlo) & (q <= c.xhi))) {
+        if (is_per<GEO>(g)) {
+          if (!isfinite(lon)) return nan ? nan : 1;
+          if (!(q >= x0 && q < x0 + 360.0f)) q = wrap_lon(lon, x0);
+        } else if (!(lon >= x0 && lon <= axis_hi(g, 0, lon))) {
+          return nan ? nan : 1;
+        }
+        c.dirty |= 1;
+        if (is_per<GEO>(g) && q >= axis_hi(g, 0, q)) {   // the wrap cell
+          c.ci = g.nx - 1;
+          c.xlo = axis_hi(g, 0, q);
+          c.xhi = lon_end(g, q);
+          c.rx = __frcp_rn(c.xhi - c.xlo);
+        } else {
+          relocate32(g, 0, g.nx, q, c.ci, c.xlo, c.xhi, c.rx);
+        }
+      }
+      if (!((lat >= c.ylo) & (lat <= c.yhi))) {
+        if (!(lat >= axis_lo(g, 1, lat) && lat <= axis_hi(g, 1, lat))) return nan ? nan : 1;
+        c.dirty |= 1;
+        relocate32(g, 1, g.ny, lat, c.cj, c.ylo, c.yhi, c.ry);
+      }
       if constexpr (D3) {
-        if (!locate_axis<float>(g, 2, g.nz, c.ck, c.zlo, c.zhi, c.rz, dep, zeta, c.dirty))
-          return nan ? nan : 2;
+        if (!((dep >= c.zlo) & (dep <= c.zhi))) {
+          if (!(dep >= axis_lo(g, 2, dep) && dep <= axis_hi(g, 2, dep))) return nan ? nan : 2;
+          c.dirty |= 1;
+          relocate32(g, 2, g.nz, dep, c.ck, c.zlo, c.zhi, c.rz);
+        }
       } else {
         c.ck = 0;
       }
       if (refresh32(a, c, ck, off)) return -1;
-      if (is_per<GEO>(g)) q = wrap_lon(lon, x0);
     }
     xi = (q - c.xlo) * c.rx;
     eta = (lat - c.ylo) * c.ry;

@@ -14,6 +14,7 @@ enum DevErr : int {
   DEVERR_NONE = 0,
   DEVERR_SLAB_MISSING = 1,   // a kernel needed a snapshot that is not resident
   DEVERR_TIME_RANGE = 2,     // a stage time fell outside a non-periodic field
+  DEVERR_CELL_INDEX = 3,     // a corner gather was asked for a cell outside the grid
 };
 
 struct GridArgs {
