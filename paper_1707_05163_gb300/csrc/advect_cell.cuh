@@ -49,10 +49,14 @@ __device__ __forceinline__ int velocity_cell(const StepArgs &a, Sampler<float, S
   const GridArgs &g = a.g;
   int i = b.i, j = b.j, k = b.k;
   float x = b.x + kc[0] * off, y = b.y + kc[1] * off, z = D3 ? b.z + kc[2] * off : 0.f;
-  if (!norm_axis(i, x, g.nx, is_per<GEO>(g))) return 1;
-  if (!norm_axis(j, y, g.ny, false)) return 1;
+  // No NaN test on the stage velocity: a NaN velocity makes the next stage
+  // offset (or the step's result) NaN, which fails normalisation, and a
+  // failure on a NaN offset reports PG_NAN, with the state kept.
+  const int nan = (!(x == x) | !(y == y) | !(z == z)) ? 3 : 0;
+  if (!norm_axis(i, x, g.nx, is_per<GEO>(g))) return nan ? nan : 1;
+  if (!norm_axis(j, y, g.ny, false)) return nan ? nan : 1;
   if constexpr (D3) {
-    if (!norm_axis(k, z, g.nz, false)) return 2;
+    if (!norm_axis(k, z, g.nz, false)) return nan ? nan : 2;
   }
   if (i != c.ci || j != c.cj || (D3 && k != c.ck)) {
     c.ci = i;
@@ -60,8 +64,8 @@ __device__ __forceinline__ int velocity_cell(const StepArgs &a, Sampler<float, S
     c.ck = D3 ? k : 0;
     c.dirty |= 1;
   }
-  const int r = sample_fields(a, c, ck, off, x, y, z, vel);
-  if (r) return r;
+  if (refresh32(a, c, ck, off)) return -1;
+  interp32<Store, NF, D3, GEO, false>(c, x, y, z, tau32(a, c, ck, off), vel);
   if (is_sph<GEO>(g)) {
     const float lat = g.x0f[1] + ((float)j + y) * g.df[1];
     vel[0] = __fdividef(vel[0] * g.inv_m[0], cos_deg(lat));
@@ -84,17 +88,15 @@ __device__ __forceinline__ int step_cell(const StepArgs &a, Sampler<float, Store
   const float half = 0.5f * h;
   const int nst = a.k.scheme == 0 ? 1 : 4;
   int r;
+  acc[0] = 0.f; acc[1] = 0.f; acc[2] = 0.f;
 #pragma unroll 1
   for (int q = 0; q < nst; ++q) {
-    const float off = q == 0 ? 0.f : (q == 3 ? h : half);
+    const float off = (q == 0 ? 0.f : (q == 3 ? 1.f : 0.5f)) * h;
     if ((r = velocity_cell(a, c, ck, off, s, kc, kc))) return r;
-    if (q == 0) {
-      acc[0] = kc[0]; acc[1] = kc[1]; acc[2] = kc[2];
-    } else if (q == 3) {
-      acc[0] += kc[0]; acc[1] += kc[1]; acc[2] += kc[2];
-    } else {
-      acc[0] += 2.f * kc[0]; acc[1] += 2.f * kc[1]; acc[2] += 2.f * kc[2];
-    }
+    const float wg = (q == 1 || q == 2) ? 2.f : 1.f;
+    acc[0] = fmaf(wg, kc[0], acc[0]);
+    acc[1] = fmaf(wg, kc[1], acc[1]);
+    acc[2] = fmaf(wg, kc[2], acc[2]);
   }
   const float w = nst == 1 ? h : h * (1.0f / 6.0f);
   CellState n = s;
@@ -111,6 +113,8 @@ __device__ __forceinline__ int step_cell(const StepArgs &a, Sampler<float, Store
     n.y += sigma * n2 * g.inv_m[1];
   }
   if (D3 && (a.k.beh & 2u)) n.z += a.k.w_sink_f * h * g.inv_m[2];
+  // a NaN result comes from a NaN stage velocity (see velocity_cell)
+  if (!(n.x == n.x) | !(n.y == n.y) | !(n.z == n.z)) return 3;
   if (!norm_axis(n.i, n.x, g.nx, is_per<GEO>(g))) return 1;
   if (!norm_axis(n.j, n.y, g.ny, false)) return 1;
   if constexpr (D3) {
@@ -121,7 +125,10 @@ __device__ __forceinline__ int step_cell(const StepArgs &a, Sampler<float, Store
 }
 
 template <typename Store, int NF, bool D3, int GEO>
-__global__ void __launch_bounds__(256, 2) advect_cell_kernel(StepArgs a) {
+// 3-D: at most 128 registers (two 256-thread blocks per SM).  2-D, with a
+// third of the corner values: at most 85 registers, six 128-thread blocks
+// (24 warps) per SM, measured faster than five or four.
+__global__ void __launch_bounds__(D3 ? 256 : 128, D3 ? 2 : 6) advect_cell_kernel(StepArgs a) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long done = 0;
   if (p < a.p.n && a.p.status[p] == 0) {

@@ -350,11 +350,12 @@ __device__ __forceinline__ void count_steps(unsigned long long done, unsigned lo
   if ((threadIdx.x & 31) == 0 && done) atomicAdd(counter, done);
 }
 
-// FP32: at most 128 registers (two 256-thread blocks per SM); measured
+// FP32 3-D: at most 128 registers (two 256-thread blocks per SM); measured
 // faster than the unbounded allocation despite a few spilled words, as more
-// resident warps hide the gather and dependency latencies.
+// resident warps hide the gather and dependency latencies.  FP32 2-D: at most
+// 85 registers, six 128-thread blocks (24 warps) per SM.
 template <typename Real, typename Store, int NF, bool D3, int GEO>
-__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1) advect_plain_kernel(StepArgs a) {
+__global__ void __launch_bounds__(sizeof(Real) == 4 && !D3 ? 128 : 256, sizeof(Real) == 4 ? (D3 ? 2 : 6) : 1) advect_plain_kernel(StepArgs a) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long done = 0;
   if (p < a.p.n && a.p.status[p] == 0) done = advance_particle<Real, Store, NF, D3, GEO>(a, p);
