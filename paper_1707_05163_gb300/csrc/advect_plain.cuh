@@ -242,7 +242,13 @@ __device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, 
     }
   }
   Real nlon, nlat, ndep;
-  if (nst == 1) {
+  if constexpr (sizeof(Real) == 4) {
+    // FP32: (k1 + 2 k2 + 2 k3 + k4) h / 6 with h / 6 formed once (no division)
+    const float w = nst == 1 ? hr : hr * (1.0f / 6.0f);
+    nlon = fmaf(acc[0], w, lon);
+    nlat = fmaf(acc[1], w, lat);
+    ndep = fmaf(acc[2], w, dep);
+  } else if (nst == 1) {
     nlon = lon + acc[0] * hr;
     nlat = lat + acc[1] * hr;
     ndep = dep + acc[2] * hr;
