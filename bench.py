@@ -66,6 +66,24 @@ def parse():
     return ap.parse_args()
 
 
+def reduce_over_ranks(elapsed_ms, particle_steps, device):
+    """Whole-job timing under torchrun: the maximum of the ranks' timed regions
+    and the sum of their particle-steps.  Each rank advects its own particles
+    (weak scaling, no data-path collective); this reduction is the only
+    collective of the run."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(elapsed_ms), float(particle_steps)
+    t = torch.tensor([float(elapsed_ms), float(particle_steps)], device=device,
+                     dtype=torch.float64)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -276,16 +294,7 @@ def main():
     c1 = C.c_int64()
     lib.pg_launch_count(C.byref(c1))
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed_ms, float(total_steps)], device=dev, dtype=torch.float64)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        elapsed_ms, total_all = float(mx[0]), float(sm[1])
-    else:
-        total_all = float(total_steps)
+    elapsed_ms, total_all = reduce_over_ranks(elapsed_ms, total_steps, dev)
     value = total_all / (elapsed_ms / 1e3)
 
     # end-to-end through the C ABI from host buffers
