@@ -514,7 +514,7 @@ def surrogate_workload(args, rank, world, local):
     line = {
         "metric": METRIC, "value": main["equivalent_rate"], "unit": UNIT, "n_gpus": 1,
         "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16 MLP (fp32 accumulate) + f32 RK4 judge",
+        "vs_baseline": None, "dtype": "bf16 MLP (fp32 accumulate) + f32 RK4 check",
         "data": "synthetic (seeded k^-3 random streamfunction field, uniform particles)",
         "config": {"workload": f"surrogate: MLP 37-256x4-3 trained on {args.train_segments} RK4 "
                                f"24 h segments, {n} particles x {nsteps} days, RK4 check every 5 "

@@ -310,12 +310,12 @@ typedef struct {
 } pg_surrogate_stats;
 
 /* Surrogate run: `nsteps` network steps of `horizon` seconds in blocks of
- * `check_every`.  The last step of every block is judged by RK4 with steps of
- * dt_check from the same state: particles whose position differs by more than
- * `threshold` cells (depth: layers), and particles that the network or the
- * judge deleted within the block, are re-integrated with RK4 from the start
- * of the block; all others take RK4's state for the judged step.  The kernel
- * `k` is the RK4 of the judge. */
+ * `check_every`.  The last step of every block is checked against RK4 with
+ * steps of dt_check from the same state: particles whose position differs by
+ * more than `threshold` cells (depth: layers), and particles that the network
+ * or the checking RK4 deleted within the block, are re-integrated with RK4
+ * from the start of the block; all others take RK4's state for the checked
+ * step.  The kernel `k` is the checking RK4's. */
 PG_API pg_status pg_surrogate_run(pg_pset *ps, pg_mlp *net, const pg_kernel *k, int nsteps,
                                   int check_every, double horizon, double dt_check,
                                   double threshold, pg_surrogate_stats *stats, void *stream);

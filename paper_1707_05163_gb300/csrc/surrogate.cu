@@ -153,7 +153,7 @@ __global__ void displacement_kernel(GridArgs g, const float *lon0, const float *
 
 // Position error (in cells; depth in units of the local layer) between the
 // network's state and RK4's; rejects particles above the threshold, and any
-// particle alive at the block's start that the network or the judge deleted
+// particle alive at the block's start that the network or the checking RK4 deleted
 // within the block (RK4 from the block's start then decides).  err_sum[0] +=
 // error over particles both keep alive, err_sum[1] += count.
 __global__ void check_kernel(GridArgs g, const float *lon_a, const float *lat_a,
@@ -438,7 +438,7 @@ pg_status pg_surrogate_run(pg_pset *ps, pg_mlp *net, const pg_kernel *k, int nst
     S.checked += (int64_t)h_esum[1];
     S.error_sum += h_esum[0];
     S.rejected += (int64_t)h_nrej;
-    // everyone takes RK4's state for the judged step ...
+    // everyone takes RK4's state for the checked step ...
     if ((e = copy_set(ps, chk))) { r = PG_ERR_CUDA; set_error("%s", cudaGetErrorString(e)); break; }
     // ... and the rejected re-integrate the whole block from the checkpoint
     if (h_nrej > 0) {

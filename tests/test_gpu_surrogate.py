@@ -1,5 +1,5 @@
 """The flow-map surrogate: features, displacements, training, and the run in
-which RK4 judges the network and takes over for rejected particles."""
+which RK4 checks the network and takes over for rejected particles."""
 import numpy as np
 import pytest
 
