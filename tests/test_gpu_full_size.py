@@ -1,0 +1,99 @@
+"""Parity at the full size of the 3-D workload, in the launch configuration
+bench.py times: 10M particles in the upper 1000 m of a global 1/4-degree grid
+(1440 x 720 x 50, 30 daily snapshots, periodic in time and longitude), FP32
+RK4 with dt 30 min, block 128, 288-step chunks and Morton re-sort every 288
+steps.  The FP64 oracle advances a seeded sample of the same particles one by
+one through the same field.
+
+Pass/fail is at 24 h (from the same start states): mean position error below
+1e-3 cell.  Over the full 30 days the flow is chaotic and FP32 and FP64 paths
+separate slowly; there the test asks for equal statuses on nearly all sampled
+particles and a small mean error.
+"""
+import numpy as np
+import pytest
+
+import bench
+import oracle as O
+import synth
+from tests.helpers import DAY
+
+pytestmark = pytest.mark.gpu
+
+N = 10_000_000
+SAMPLE = 4096
+
+
+def _cell_error(g_lon, g_lat, g_dep, o_lon, o_lat, o_dep, gf):
+    dx = 360.0 / gf.nx
+    dy = 180.0 / gf.ny
+    dlon = (g_lon - o_lon + 180.0) % 360.0 - 180.0
+    k = np.clip(np.searchsorted(gf.depth, o_dep) - 1, 0, gf.nz - 2)
+    dz = gf.depth[k + 1] - gf.depth[k]
+    return np.maximum(np.maximum(np.abs(dlon) / dx, np.abs(g_lat - o_lat) / dy),
+                      np.abs(g_dep - o_dep) / dz)
+
+
+@pytest.fixture(scope="module")
+def pg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1707_05163_gb300 as pg
+    pg.load()
+    return pg
+
+
+@pytest.fixture(scope="module")
+def workload(pg):
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    gf = synth.GlobalField(res_deg=0.25, nz=50, nt=30, seed=2, period=30 * DAY)
+    host = torch.empty((len(gf.times), gf.nfields, gf.nz, gf.ny, gf.nx), dtype=torch.float32)
+    fs = bench.build_fieldset_device(pg, gf, torch, dev, bench.make_field_host_bases(gf), host)
+    lon, lat, dep = synth.uniform_particles(N, 2, (0.0, 360.0), (-80.0, 80.0), (5.0, 1000.0),
+                                            dtype=np.float32)
+    field = O.Field(gf.lon, gf.lat, gf.depth, gf.times, host.numpy(), 1, True, gf.period)
+    ids = np.sort(np.random.default_rng(11).choice(N, SAMPLE, replace=False))
+    return dict(torch=torch, dev=dev, gf=gf, fs=fs, lon=lon, lat=lat, dep=dep, field=field,
+                ids=ids)
+
+
+def _gpu_and_oracle(pg, w, days):
+    torch = w["torch"]
+    ps = pg.ParticleSet(w["fs"], torch.from_numpy(w["lon"]).to(w["dev"]),
+                        torch.from_numpy(w["lat"]).to(w["dev"]),
+                        torch.from_numpy(w["dep"]).to(w["dev"]), pos="f32", seed=0)
+    ps.set_tune(128, 288, 288)
+    steps = ps.execute(pg.Kernel("rk4"), days * DAY, 1800.0)
+    g = ps.get()
+    ps.destroy()
+    ids = w["ids"]
+    gs = {k: v[ids] for k, v in g.items()}      # get() sorts by id; ids are 0..N-1
+    np.testing.assert_array_equal(gs["id"], ids)
+    n = len(ids)
+    st = [w["lon"][ids].astype(np.float64), w["lat"][ids].astype(np.float64),
+          w["dep"][ids].astype(np.float64), np.zeros(n), ids.astype(np.uint64),
+          np.zeros(n, np.uint32), np.zeros(n, np.uint8)]
+    O.run(w["field"], O.Kernel(O.RK4), *st, 1800.0, days * DAY, days * DAY)
+    return steps, gs, st
+
+
+def test_full_size_24h_within_1e3_cell(pg, workload):
+    steps, g, st = _gpu_and_oracle(pg, workload, 1.0)
+    assert steps > 0.99 * N * 48
+    np.testing.assert_array_equal(g["status"], st[6])
+    alive = st[6] == 0
+    assert alive.mean() > 0.99
+    np.testing.assert_array_equal(g["step"][alive], 48)
+    e = _cell_error(g["lon"], g["lat"], g["depth"], st[0], st[1], st[2], workload["gf"])[alive]
+    assert e.mean() < 1e-3, e.mean()
+
+
+def test_full_size_30_days_statuses_and_drift(pg, workload):
+    steps, g, st = _gpu_and_oracle(pg, workload, 30.0)
+    assert steps > 0.9 * N * 1440
+    assert np.mean(g["status"] == st[6]) > 0.99
+    both = (g["status"] == 0) & (st[6] == 0)
+    e = _cell_error(g["lon"], g["lat"], g["depth"], st[0], st[1], st[2], workload["gf"])[both]
+    assert np.median(e) < 2e-2, (np.median(e), e.mean())
