@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--train-segments", type=int, default=20_000_000)
     ap.add_argument("--train-steps", type=int, default=20000)
     ap.add_argument("--sur-days", type=float, default=180.0)
-    ap.add_argument("--tcgen05", action="store_true", help="surrogate GEMMs on tcgen05")
+    ap.add_argument("--engine", default="tcgen05", choices=["tcgen05", "mma.sync"],
+                    help="tensor-core engine of the surrogate's forward GEMMs")
     ap.add_argument("--storage", default="f16", choices=["f16", "bf16"])
     return ap.parse_args()
 
@@ -443,8 +444,7 @@ def surrogate_workload(args, rank, world, local):
     t_data = time.perf_counter() - t0
     xv, yv = S.make_segments(fs, 1_000_000, seed=6, groups=20, period=gf.period)
     net = pg.MLP(37, 256, 4, 3, seed=5)
-    if args.tcgen05:
-        net.set_engine(True)
+    net.set_engine(args.engine == "tcgen05")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     losses = S.train(net, x, y, steps=args.train_steps, batch=16384, lr=1e-3)
@@ -467,7 +467,7 @@ def surrogate_workload(args, rank, world, local):
         ms = (time.perf_counter() - t0) / 3 * 1e3
         engines[name] = {"ms_per_10M_rows": ms, "TFLOPs": flop_row * 1e7 / (ms * 1e-3) / 1e12}
     del xb
-    net.set_engine(bool(args.tcgen05))
+    net.set_engine(args.engine == "tcgen05")
     pred = net.forward(xv)
     err = (pred[:, :2] - yv[:, :2]).abs().max(dim=1).values.cpu().numpy()
     held = {"mean_cells": float(err.mean()), "median_cells": float(np.median(err)),
@@ -519,7 +519,7 @@ def surrogate_workload(args, rank, world, local):
         "config": {"workload": f"surrogate: MLP 37-256x4-3 trained on {args.train_segments} RK4 "
                                f"24 h segments, {n} particles x {nsteps} days, RK4 check every 5 "
                                "steps, fallback above 1e-3 cell, 3-D 1/4 deg field",
-                   "engine": "tcgen05" if args.tcgen05 else "mma.sync",
+                   "engine": args.engine,
                    "value": "equivalent RK4 particle-steps/s (48 steps of 30 min per day)"},
         "plain_fp32_rk4_rate": rk_steps / t_rk,
         "speedup_vs_plain_fp32": main["speedup_vs_plain_rk4"],

@@ -55,6 +55,19 @@ __host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
          ((uint32_t)(m >> 4) << 24);
 }
 
+// 16 FP32 values rounded to BF16 (nearest even, in pairs) and written as two
+// 16-byte stores; dst must be 16-byte aligned.
+__device__ __forceinline__ void store_bf16x16(__nv_bfloat16 *dst, const float (&v)[16]) {
+  uint32_t w[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    w[j] = *reinterpret_cast<const uint32_t *>(&h);
+  }
+  reinterpret_cast<uint4 *>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  reinterpret_cast<uint4 *>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
 // copy rows [0, rows) of a K-wide BF16 matrix (row stride ld) into the
 // core-matrix layout; rows in [rows, R) are zero-filled
 template <int K>
@@ -162,18 +175,30 @@ gemm_tc_kernel(const __nv_bfloat16 *__restrict__ A, int lda, const __nv_bfloat16
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n");
       if (row < M) {
+        // 16 consecutive columns of this thread's row: 16-byte vector loads
+        // of the bias and 16-byte stores (32 B of BF16 or 64 B of FP32)
         const size_t o = (size_t)row * ldc + c0;
+        float v[16];
 #pragma unroll
-        for (int j = 0; j < 16; j += 2) {
-          float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
-          if (bias) { v0 += bias[c0 + j]; v1 += bias[c0 + j + 1]; }
-          if (pre_bf16)
-            *reinterpret_cast<__nv_bfloat162 *>(pre_bf16 + o + j) = __floats2bfloat162_rn(v0, v1);
-          if (act == 1) { v0 = gelu_tc(v0); v1 = gelu_tc(v1); }
-          if (out_f32) { out_f32[o + j] = v0; out_f32[o + j + 1] = v1; }
-          if (out_bf16)
-            *reinterpret_cast<__nv_bfloat162 *>(out_bf16 + o + j) = __floats2bfloat162_rn(v0, v1);
+        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+        if (bias) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4) {
+            const float4 b4 = *reinterpret_cast<const float4 *>(bias + c0 + j);
+            v[j] += b4.x; v[j + 1] += b4.y; v[j + 2] += b4.z; v[j + 3] += b4.w;
+          }
         }
+        if (pre_bf16) store_bf16x16(pre_bf16 + o, v);
+        if (act == 1) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = gelu_tc(v[j]);
+        }
+        if (out_f32) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            *reinterpret_cast<float4 *>(out_f32 + o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+        if (out_bf16) store_bf16x16(out_bf16 + o, v);
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -213,14 +238,16 @@ cudaError_t launch_tc(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, i
 }  // namespace
 
 // Forward products of the MLP on tcgen05; N and K must be 64 or 256, all row
-// strides multiples of 8 elements.  *err (device) is set to 1 if a CTA gave
+// strides multiples of 8 elements, bias and outputs 16-byte aligned.  *err (device) is set to 1 if a CTA gave
 // up waiting for its accumulator.
 cudaError_t gemm_nt_tc(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
                        int64_t M, int N, int K, const float *bias, int act, float *out_f32,
                        __nv_bfloat16 *out_bf16, __nv_bfloat16 *pre_bf16, int ldc, cudaStream_t st,
                        int *err) {
   if (M == 0) return cudaSuccess;
-  if (lda % 8 || ldb % 8 || ldc % 2 || !err) return cudaErrorInvalidValue;
+  if (lda % 8 || ldb % 8 || ldc % 8 || !err) return cudaErrorInvalidValue;
+  if (((uintptr_t)bias | (uintptr_t)out_f32 | (uintptr_t)out_bf16 | (uintptr_t)pre_bf16) % 16)
+    return cudaErrorInvalidValue;
   if (N == 256 && K == 256)
     return launch_tc<256, 256>(A, lda, B, ldb, M, bias, act, out_f32, out_bf16, pre_bf16, ldc, st, err);
   if (N == 256 && K == 64)
