@@ -179,19 +179,18 @@ __global__ void __launch_bounds__(kThreads) gemm_nt_mma(const __nv_bfloat16 *__r
         float v0 = acc[i][j][h * 2 + 0], v1 = acc[i][j][h * 2 + 1];
         if (ep.bias) { v0 += ep.bias[col]; v1 += ep.bias[col + 1]; }
         const size_t o = (size_t)row * ep.ldc + col;
-        if (ep.pre_bf16) {
-          ep.pre_bf16[o] = __float2bfloat16_rn(v0);
-          ep.pre_bf16[o + 1] = __float2bfloat16_rn(v1);
-        }
+        // column pairs as single 4-byte (BF16) and 8-byte (FP32) stores
+        // (col and ldc are even)
+        if (ep.pre_bf16)
+          *reinterpret_cast<__nv_bfloat162 *>(ep.pre_bf16 + o) = __floats2bfloat162_rn(v0, v1);
         if (ep.act == 1) { v0 = gelu(v0); v1 = gelu(v1); }
         if (ep.out_f32) {
-          if (ep.accumulate) { ep.out_f32[o] += v0; ep.out_f32[o + 1] += v1; }
-          else { ep.out_f32[o] = v0; ep.out_f32[o + 1] = v1; }
+          float2 *d = reinterpret_cast<float2 *>(ep.out_f32 + o);
+          if (ep.accumulate) { const float2 c = *d; v0 += c.x; v1 += c.y; }
+          *d = make_float2(v0, v1);
         }
-        if (ep.out_bf16) {
-          ep.out_bf16[o] = __float2bfloat16_rn(v0);
-          ep.out_bf16[o + 1] = __float2bfloat16_rn(v1);
-        }
+        if (ep.out_bf16)
+          *reinterpret_cast<__nv_bfloat162 *>(ep.out_bf16 + o) = __floats2bfloat162_rn(v0, v1);
       }
 }
 
@@ -317,7 +316,9 @@ cudaError_t gemm_nt(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int
                     __nv_bfloat16 *out_bf16, __nv_bfloat16 *pre_bf16, int ldc, int accumulate,
                     cudaStream_t st) {
   if (M == 0) return cudaSuccess;
-  if (N % BN || K % BK) return cudaErrorInvalidValue;
+  if (N % BN || K % BK || ldc % 2) return cudaErrorInvalidValue;
+  if (((uintptr_t)out_f32 % 8) || ((uintptr_t)out_bf16 % 4) || ((uintptr_t)pre_bf16 % 4))
+    return cudaErrorInvalidValue;
   GemmEpi ep{bias, act, out_f32, out_bf16, pre_bf16, ldc, accumulate};
   dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)(N / BN));
   gemm_nt_mma<<<grid, kThreads, 0, st>>>(A, lda, B, ldb, (int)M, N, K, ep);
