@@ -3,11 +3,12 @@
 // out[M x N] = act(A[M x K] . B[N x K]^T + bias), BF16 operands, FP32
 // accumulation in tensor memory (TMEM), N and K in {64, 256}.  Persistent
 // CTAs (one per SM): each loads B once into shared memory and then walks
-// 128-row tiles of A.  Per tile: the 128 threads copy the A tile into shared
-// memory, one thread issues K/16 tcgen05.mma (128 x N x 16) and commits them
-// to an mbarrier, all threads wait on it (bounded), then each warp reads its
-// 32 accumulator rows from TMEM (tcgen05.ld) and applies bias, GELU and the
-// BF16/FP32 stores.
+// 128-row tiles of A.  Per tile: one thread issues K/16 tcgen05.mma (128 x N
+// x 16) on the A tile in shared memory and commits them to an mbarrier, all
+// threads wait on it (bounded), start copying the next A tile into the now
+// free buffer (cp.async), and meanwhile each warp reads its 32 accumulator
+// rows from TMEM (tcgen05.ld) and applies bias, GELU and the BF16/FP32
+// stores.
 //
 // Shared-memory operand layout (K-major, no swizzle): 8-row x 16-byte core
 // matrices; core matrix (row group g, 16-byte K chunk c) sits at byte
@@ -118,11 +119,16 @@ gemm_tc_kernel(const __nv_bfloat16 *__restrict__ A, int lda, const __nv_bfloat16
   uint32_t phase = 0;
   bool failed = false;
 
+  // The A tile of the next iteration is copied while this tile's epilogue
+  // runs: once the MMA has completed (mbarrier), the shared A buffer is free.
+  auto copy_a = [&](int64_t t) {
+    const int64_t m = t * TM;
+    load_tile<K>(sA, A + (size_t)m * lda, lda, (int)((M - m) < TM ? (M - m) : TM), TM);
+    asm volatile("cp.async.commit_group;\n");
+  };
+  if ((int64_t)blockIdx.x < ntiles) copy_a(blockIdx.x);
   for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     const int64_t m0 = tile * TM;
-    const int rows = (int)((M - m0) < TM ? (M - m0) : TM);
-    load_tile<K>(sA, A + (size_t)m0 * lda, lda, rows, TM);
-    asm volatile("cp.async.commit_group;\n");
     asm volatile("cp.async.wait_group 0;\n");
     asm volatile("fence.proxy.async.shared::cta;\n");
     __syncthreads();
@@ -160,6 +166,7 @@ gemm_tc_kernel(const __nv_bfloat16 *__restrict__ A, int lda, const __nv_bfloat16
     }
     phase ^= 1u;
     if (failed) break;
+    if (tile + gridDim.x < ntiles) copy_a(tile + gridDim.x);
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     const int64_t row = m0 + warp * 32 + lane;
 #pragma unroll 1
