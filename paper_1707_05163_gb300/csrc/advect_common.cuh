@@ -244,8 +244,8 @@ __device__ __forceinline__ int snap_next(const FieldArgs &f, int s0) {
   return s0 + 1 < f.nt ? s0 + 1 : 0;
 }
 
-template <typename Real, typename Store, int NF, bool D3, int GEO>
-__device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Store, NF, D3, GEO> &c,
+template <typename Real, typename Store, int NF, bool D3, int GEO, class A>
+__device__ __forceinline__ bool gather_slab(const A &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                             int sl, int s) {
   const GridArgs &g = a.g;
   const Store *base = reinterpret_cast<const Store *>(a.f.tab[s]);
@@ -287,8 +287,8 @@ __device__ __forceinline__ bool gather_slab(const StepArgs &a, Sampler<Real, Sto
 // Make `v` hold the corners of the cached cell for snapshots s0 and s1.  If
 // only the snapshot pair moved on by one, the shared snapshot's corners move
 // from slot 1 to slot 0 and only the new snapshot is read.
-template <typename Real, typename Store, int NF, bool D3, int GEO>
-__device__ __forceinline__ bool gather(const StepArgs &a, Sampler<Real, Store, NF, D3, GEO> &c,
+template <typename Real, typename Store, int NF, bool D3, int GEO, class A>
+__device__ __forceinline__ bool gather(const A &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                        bool steady) {
   if (steady) {
     if (!gather_slab(a, c, 0, c.s0)) return false;
@@ -363,8 +363,8 @@ __device__ __forceinline__ float w_of(const KernArgs &k, float) { return k.w_sin
 // FP32 offset inside the cached interval; the FP64 step start is formed only
 // when a stage leaves it.  Returns 0, or -1 for an internal failure recorded
 // in a.err.
-template <typename Store, int NF, bool D3, int GEO>
-__device__ __forceinline__ int refresh32(const StepArgs &a, Sampler<float, Store, NF, D3, GEO> &c,
+template <typename Store, int NF, bool D3, int GEO, class A>
+__device__ __forceinline__ int refresh32(const A &a, Sampler<float, Store, NF, D3, GEO> &c,
                                          Clock &ck, float off) {
   const bool steady = a.f.nt == 1;
   if (!steady) {
@@ -396,8 +396,8 @@ __device__ __forceinline__ int refresh32(const StepArgs &a, Sampler<float, Store
 
 // FP32 time weight of the stage inside the cached interval (0 for a steady
 // field).
-template <typename Store, int NF, bool D3, int GEO>
-__device__ __forceinline__ float tau32(const StepArgs &a, const Sampler<float, Store, NF, D3, GEO> &c,
+template <typename Store, int NF, bool D3, int GEO, class A>
+__device__ __forceinline__ float tau32(const A &a, const Sampler<float, Store, NF, D3, GEO> &c,
                                        const Clock &ck, float off) {
   return a.f.nt == 1 ? 0.f : fminf((ck.d + off) * c.rspan, 1.0f);
 }
@@ -461,8 +461,8 @@ __device__ __forceinline__ int interp32(const Sampler<float, Store, NF, D3, GEO>
 // (step start + off), corner gather if the cell or interval changed, spatial
 // interpolation in each snapshot, then linear interpolation in time.
 // Returns 0, PG_NAN (3), or -1 for an internal failure recorded in a.err.
-template <typename Real, typename Store, int NF, bool D3, int GEO>
-__device__ __forceinline__ int sample_fields(const StepArgs &a, Sampler<Real, Store, NF, D3, GEO> &c,
+template <typename Real, typename Store, int NF, bool D3, int GEO, class A>
+__device__ __forceinline__ int sample_fields(const A &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                              Clock &ck, Real off, Real xi, Real eta, Real zeta,
                                              Real (&vel)[3]) {
   if constexpr (sizeof(Real) == 4) {

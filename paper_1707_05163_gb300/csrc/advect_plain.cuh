@@ -106,8 +106,8 @@ __device__ __forceinline__ void relocate32(const GridArgs &g, int a, int n, floa
 // Velocity in position units per second at a stage (stage time = step start
 // + off).  Returns 0 or a particle status (PG_OOB_*, PG_NAN); -1 for an
 // internal failure already recorded in a.err.
-template <typename Real, typename Store, int NF, bool D3, int GEO>
-__device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, NF, D3, GEO> &c,
+template <typename Real, typename Store, int NF, bool D3, int GEO, class A>
+__device__ __forceinline__ int velocity(const A &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                         Clock &ck, Real off, Real lon, Real lat, Real dep,
                                         Real (&vel)[3]) {
   const GridArgs &g = a.g;
@@ -196,8 +196,8 @@ __device__ __forceinline__ int velocity(const StepArgs &a, Sampler<Real, Store, 
 // One step of Eq. 1.  Returns 0 and updates (lon, lat, dep) on success.
 // RK4 stages run in a loop: stage s samples at (X + k_{s-1} c_s h, t + c_s h)
 // with c = (0, 1/2, 1/2, 1) and accumulates ((k1 + 2 k2) + 2 k3) + k4.
-template <typename Real, typename Store, int NF, bool D3, int GEO>
-__device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, NF, D3, GEO> &c,
+template <typename Real, typename Store, int NF, bool D3, int GEO, class A>
+__device__ __forceinline__ int step_one(const A &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                         Clock &ck, Real &lon, Real &lat, Real &dep, Real hr,
                                         const uint64_t *idp, uint32_t stp) {
   Real kc[3] = {(Real)0, (Real)0, (Real)0};
@@ -285,8 +285,8 @@ __device__ __forceinline__ int step_one(const StepArgs &a, Sampler<Real, Store, 
 // The chunk kernel: each thread advances one particle while its time is
 // before t_stop and t_end (in the direction of dt), shortening only the step
 // that lands on t_end.  Returns the number of steps taken.
-template <typename Real, typename Store, int NF, bool D3, int GEO>
-__device__ __forceinline__ unsigned long long advance_particle(const StepArgs &a, int64_t p) {
+template <typename Real, typename Store, int NF, bool D3, int GEO, class A>
+__device__ __forceinline__ unsigned long long advance_particle(const A &a, int64_t p) {
   unsigned long long done = 0;
   {
     Real *X = reinterpret_cast<Real *>(a.p.x);
@@ -391,34 +391,43 @@ struct BatchArgs {
   int *err;
 };
 
-// The argument block of the current tile's release is assembled once per
-// tile in shared memory, which every thread of the tile then reads.
+// The step's arguments as the batch kernel sees them: the grid and the field
+// refer to the kernel's parameters (constant bank), the release's kernel and
+// particle arrays to the copy the tile's first thread made in shared memory.
+struct BatchStep {
+  const GridArgs &g;
+  const FieldArgs &f;
+  const KernArgs &k;
+  const PartArgs &p;
+  double dt, t_stop, t_end;
+  unsigned long long *steps_done;
+  int *err;
+};
+
 template <typename Store, int NF, bool D3, int GEO>
-__global__ void __launch_bounds__(256, 2) advect_batch_kernel(BatchArgs b) {
+__global__ void __launch_bounds__(256, 2) advect_batch_kernel(const __grid_constant__ BatchArgs b) {
   __shared__ int tile;
-  __shared__ StepArgs sa;
+  __shared__ KernArgs sk;
+  __shared__ PartArgs sp;
+  __shared__ double sdt, st_end;
   unsigned long long done = 0;
   for (;;) {
     if (threadIdx.x == 0) {
       tile = atomicAdd(b.next_tile, 1);
       if (tile < b.ntiles) {
         const BatchRelease *R = b.rel + b.tiles[tile].x;
-        sa.g = b.g;
-        sa.f = b.f;
-        sa.k = R->k;
-        sa.p = R->p;
-        sa.dt = R->dt;
-        sa.t_stop = b.t_stop;
-        sa.t_end = R->t_end;
-        sa.steps_done = b.steps_done;
-        sa.err = b.err;
+        sk = R->k;
+        sp = R->p;
+        sdt = R->dt;
+        st_end = R->t_end;
       }
     }
     __syncthreads();
     const int t = tile;
     if (t >= b.ntiles) break;
+    const BatchStep v{b.g, b.f, sk, sp, sdt, b.t_stop, st_end, b.steps_done, b.err};
     const int64_t p = (int64_t)b.tiles[t].y + threadIdx.x;
-    if (p < sa.p.n && sa.p.status[p] == 0) done += advance_particle<float, Store, NF, D3, GEO>(sa, p);
+    if (p < sp.n && sp.status[p] == 0) done += advance_particle<float, Store, NF, D3, GEO>(v, p);
     __syncthreads();
   }
   count_steps(done, b.steps_done);
