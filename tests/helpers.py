@@ -2,6 +2,8 @@
 same seeded inputs and compare them."""
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 import oracle as O
@@ -85,3 +87,15 @@ def cell_error(g, o, spec, periodic=True):
         dz = spec.depth[k + 1] - spec.depth[k]
         e.append(np.abs(g["depth"] - o["depth"]) / dz)
     return np.max(np.stack(e), axis=0)
+
+
+def paper_value(key):
+    """A value the paper prints for one of its test cases, from
+    tests/golden/paper_reported_values.txt (each line cites its section)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "paper_reported_values.txt")
+    for line in open(path):
+        parts = line.split()
+        if parts and not parts[0].startswith("#") and parts[0] == key:
+            return float(parts[1])
+    raise KeyError(key)
