@@ -29,8 +29,9 @@
  *     counter (id lo, id hi, step, stream), then Box-Muller;
  *   - a step whose stage or final position leaves the domain is not applied and
  *     the particle is deleted (status != 0).
- * Parity of Philox itself is unpinned against an external known-answer vector;
- * it is pinned statistically and by bit-equality with the CUDA stream.
+ * Philox4x32-10 is pinned by the generator's published known-answer vectors;
+ * the word-to-uniform mapping of Box-Muller by a value computed by hand from
+ * one of them.
  *
  * Compiled with -ffp-contract=off so no multiply-add is fused behind our back.
  */

@@ -416,6 +416,84 @@ def test_philox_structure_and_statistics():
     assert O.normal_pair(5, 1, 3) != O.normal_pair(5, 1, 4) != O.normal_pair(6, 1, 3)
 
 
+def _philox_kat():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "philox4x32_10_kat.txt")
+    rows = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            w = [int(x, 16) for x in line.split()]
+            rows.append((w[:4], w[4:6], w[6:10]))
+    return rows
+
+
+def test_philox_known_answer_vectors():
+    """The oracle's Philox4x32-10 reproduces the published known-answer
+    vectors of the generator (all-zero, all-one and digits-of-pi inputs), so a
+    wrong multiplier, Weyl constant, round count or output word order fails."""
+    rows = _philox_kat()
+    assert len(rows) == 3
+    for ctr, key, want in rows:
+        got = [int(x) for x in O.philox4x32_10(ctr, key)]
+        assert got == want, ([hex(x) for x in got], [hex(x) for x in want])
+
+
+def test_normal_pair_word_layout_and_uniform_mapping():
+    """Box-Muller input of the reading: counter (id lo, id hi, step, 0), key
+    (seed lo, seed hi); words 0, 1 give the 53-bit integer m1 = (w0 >> 5) 2^26
+    + (w1 >> 6) and u1 = (m1 + 1) 2^-53 in (0, 1], words 2, 3 give m2 and
+    u2 = m2 2^-53.  Seed 0, id 0, step 0 is the all-zero known-answer vector,
+    so its normals follow by hand from the published output words."""
+    import math
+    w = _philox_kat()[0][2]                      # counter 0, key 0
+    m1 = ((w[0] >> 5) << 26) | (w[1] >> 6)
+    m2 = ((w[2] >> 5) << 26) | (w[3] >> 6)
+    assert m1 < 2 ** 53 and m2 < 2 ** 53
+    u1 = (m1 + 1) / 2.0 ** 53
+    u2 = m2 / 2.0 ** 53
+    r = math.sqrt(-2.0 * math.log(u1))
+    want = (r * math.cos(2.0 * math.pi * u2), r * math.sin(2.0 * math.pi * u2))
+    got = O.normal_pair(0, 0, 0)
+    np.testing.assert_allclose(got, want, rtol=1e-14, atol=0)
+    # a mapping with the word pairs swapped gives other variates
+    u1s, u2s = (m2 + 1) / 2.0 ** 53, m1 / 2.0 ** 53
+    rs = math.sqrt(-2.0 * math.log(u1s))
+    assert abs(got[0] - rs * math.cos(2.0 * math.pi * u2s)) > 1e-3
+    # the counter layout: id split into two words, the step in word 2, word 3 zero
+    seed, pid, step = 0x0123456789ABCDEF, 0xFEDCBA9876543210, 77
+    ww = [int(x) for x in O.philox4x32_10(
+        [pid & 0xFFFFFFFF, pid >> 32, step, 0], [seed & 0xFFFFFFFF, seed >> 32])]
+    a1 = ((((ww[0] >> 5) << 26) | (ww[1] >> 6)) + 1) / 2.0 ** 53
+    a2 = (((ww[2] >> 5) << 26) | (ww[3] >> 6)) / 2.0 ** 53
+    ra = math.sqrt(-2.0 * math.log(a1))
+    np.testing.assert_allclose(O.normal_pair(seed, pid, step),
+                               (ra * math.cos(2.0 * math.pi * a2), ra * math.sin(2.0 * math.pi * a2)),
+                               rtol=1e-14, atol=0)
+
+
+def test_non_finite_longitude_is_out_of_bounds():
+    """Reading: a longitude that is not a finite number is out of bounds, on a
+    periodic zonal axis too (it cannot be reduced modulo 360): the particle is
+    deleted with the horizontal status, takes no step and keeps its state."""
+    spec = synth.zonal_flow_sphere()
+    periodic = _field(spec)
+    keep = spec.lon <= 90.0
+    regional = O.Field(spec.lon[keep], spec.lat, spec.depth, spec.times, spec.data[..., keep],
+                       spec.mesh, False, 0.0)
+    for field in (periodic, regional):
+        st = _state([np.inf, -np.inf, np.nan, 10.0], [0.0, 0.0, 0.0, 0.0])
+        done = O.run(field, O.Kernel(O.RK4), st["lon"], st["lat"], st["depth"], st["time"],
+                     st["ids"], st["step"], st["status"], 300.0, 3600.0, 3600.0)
+        np.testing.assert_array_equal(st["status"], [1, 1, 1, 0])
+        assert done == 12
+        assert np.isposinf(st["lon"][0]) and np.isneginf(st["lon"][1]) and np.isnan(st["lon"][2])
+        np.testing.assert_array_equal(st["step"], [0, 0, 0, 12])
+    # a huge finite longitude is reduced exactly into [x0, x0 + 360)
+    x = O.wrap_lon(360.0 * 2 ** 40 + 12.5, 0.0)
+    assert x == 12.5
+
+
 def test_f16_quantisation_matches_numpy_round_to_nearest_even():
     rng = np.random.default_rng(4)
     v = np.concatenate([
