@@ -345,7 +345,13 @@ PG_API pg_status pg_pset_moments(const pg_pset *ps, double out[7], void *stream)
  *     PG_ERR_ARG before any work.
  *   - The first call on a device looks up that array's device address
  *     (cudaGetSymbolAddress) with the device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  With CUDA's lazy module loading (the
+ *     default) that first call is also when the array is placed in device
+ *     memory, so make it before the caller's own allocator reserves the
+ *     device's memory, or run with CUDA_MODULE_LOADING=EAGER.
+ *   - The looked-up address is kept for the life of the process: the call
+ *     does not survive cudaDeviceReset (nor does any other object of this
+ *     library).
  *   - Every call shares the array and leaves the last call's partial sums in
  *     it (each call overwrites all it reads, so nothing needs clearing).
  *     Calls whose work overlaps on the GPU, on any streams, race on it:

@@ -85,6 +85,21 @@ __device__ __forceinline__ void load_tile(uint8_t *dst, const __nv_bfloat16 *src
   }
 }
 
+// Poll the mbarrier for the given phase parity at most kSpinLimit times.
+__device__ __forceinline__ bool wait_parity_bounded(uint64_t *mbar, uint32_t phase) {
+  uint32_t done = 0;
+  long long spins = 0;
+  while (!done) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(su32(mbar)), "r"(phase));
+    if (!done && ++spins > kSpinLimit) break;
+  }
+  return done != 0;
+}
+
 template <int N, int K>
 __global__ void __launch_bounds__(kTcThreads, 1)
 gemm_tc_kernel(const __nv_bfloat16 *__restrict__ A, int lda, const __nv_bfloat16 *__restrict__ B,
@@ -147,21 +162,19 @@ gemm_tc_kernel(const __nv_bfloat16 *__restrict__ A, int lda, const __nv_bfloat16
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
               su32(mbar)));
     }
-    // wait for the accumulator (bounded)
+    // wait for the accumulator (bounded).  The CTA decides together whether
+    // the wait failed, so every thread leaves the loop at the same point and
+    // no aligned tcgen05 instruction or barrier is reached by part of it.
     {
-      uint32_t done = 0;
-      long long spins = 0;
-      while (!done) {
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(su32(mbar)), "r"(phase));
-        if (!done && ++spins > kSpinLimit) break;
-      }
-      if (!done) {
+      const bool done = wait_parity_bounded(mbar, phase);
+      failed = __syncthreads_or(!done) != 0;
+      if (failed) {
         if (threadIdx.x == 0) atomicCAS(err, 0, 1);
-        failed = true;
+        // the MMAs may still be running: give them a second bounded wait
+        // before the TMEM is released below, and let the copies in flight land
+        wait_parity_bounded(mbar, phase);
+        asm volatile("cp.async.wait_group 0;\n");
+        __syncthreads();
       }
     }
     phase ^= 1u;
@@ -224,13 +237,11 @@ cudaError_t launch_tc(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, i
                       const float *bias, int act, float *out_f32, __nv_bfloat16 *out_bf16,
                       __nv_bfloat16 *pre_bf16, int ldc, cudaStream_t st, int *err) {
   constexpr size_t smem = (size_t)N * K * 2 + (size_t)TM * K * 2 + 16;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<N, K>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // the attribute belongs to the current device's context: set it on every
+  // launch (cheap), so a first launch on another device is configured too
+  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<N, K>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -11,7 +11,10 @@
 // of allocated scratch.  Every GPU that loads the library holds that array
 // (229,376 bytes) until the process exits.  In host code the array's name is
 // only a host-side stand-in, so its device address is looked up once per
-// device with cudaGetSymbolAddress and cached.
+// device with cudaGetSymbolAddress and cached.  With lazy module loading the
+// first call on a device is also where the array is placed in device memory.
+// The cached address belongs to the device's primary context: after
+// cudaDeviceReset it is stale, as are all other objects of this library.
 #include <mutex>
 
 #include "pg_host.h"

@@ -60,7 +60,13 @@ def test_noalloc_moments_match_pset_moments_on_two_calls():
     st = torch.empty(n, dtype=torch.uint8, device=dev)
     ps.get_into(lon=x, lat=y, depth=z, status=st)
     ref2 = ps.moments()
-    got2 = noalloc(x, y, z, st, n)
+    # no library allocation may happen inside the call: every allocation of
+    # the library fails while the limit is zero
+    assert lib.pg_debug_set_alloc_limit(0) == 0
+    try:
+        got2 = noalloc(x, y, z, st, n)
+    finally:
+        lib.pg_debug_set_alloc_limit(-1)
     assert got2[0] == ref2[0] == int((st == 0).sum())
     np.testing.assert_allclose(got2, ref2, rtol=1e-12, atol=0)
     assert not np.allclose(got1, got2)
