@@ -95,11 +95,16 @@ def _close(a, b, rel=3e-2):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("engine", ["mma.sync", "tcgen05"])
 @pytest.mark.parametrize("shape", [(37, 256, 4, 3), (5, 64, 2, 3), (70, 128, 3, 40)])
-def test_forward_and_gradient_against_oracle(gpu, shape):
+def test_forward_and_gradient_against_oracle(gpu, shape, engine):
+    """Both tensor-core engines against the FP64 oracle (the tcgen05 engine
+    runs the products whose widths are 64 or 256; other widths, as in the
+    third shape, take the mma.sync products)."""
     pg, torch = gpu
     n_in, width, depth, n_out = shape
     net = pg.MLP(n_in, width, depth, n_out, seed=7)
+    net.set_engine(engine == "tcgen05")
     o = MLPOracle(n_in, width, depth, n_out)
     rng = np.random.default_rng(1)
     p = _random_params(o, rng).astype(np.float32)
