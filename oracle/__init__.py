@@ -4,7 +4,8 @@ Only the test-suite, the smoke check and the CPU-baseline leg of the benchmark
 may import this package.  The CUDA library never does.
 """
 from .oracle import (  # noqa: F401
-    ALIVE, OOB_HORIZ, OOB_DEPTH, NAN, BROWNIAN, SINK, EULER, RK4,
-    build, lib, Field, Kernel, run, sample, velocity, locate, locate_lon,
+    ALIVE, OOB_HORIZ, OOB_DEPTH, NAN, DELETED, BROWNIAN, SINK, SETTLE, AGE, SAMPLE, EULER, RK4,
+    LINEAR, NEAREST, build, lib, Field, Kernel, run, sample, sample_tracer, velocity, locate,
+    locate_lon,
     wrap_lon, philox4x32_10, normal_pair, quantise, dequantise,
 )

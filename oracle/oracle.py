@@ -17,8 +17,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "parcels_oracle.c")
 _OUT = os.path.join(_HERE, "_build", "libparcels_oracle.so")
 
-ALIVE, OOB_HORIZ, OOB_DEPTH, NAN = 0, 1, 2, 3
-BROWNIAN, SINK = 1, 2
+ALIVE, OOB_HORIZ, OOB_DEPTH, NAN, DELETED = 0, 1, 2, 3, 4
+BROWNIAN, SINK, SETTLE, AGE, SAMPLE = 1, 2, 4, 8, 16
+LINEAR, NEAREST = 0, 1
 EULER, RK4 = 0, 1
 FLAT, SPHERICAL = 0, 1
 DEG_M = 1852.0 * 60.0
@@ -46,13 +47,16 @@ class _FieldSet(C.Structure):
         ("mesh", C.c_int), ("periodic_lon", C.c_int), ("nfields", C.c_int),
         ("nt", C.c_int), ("times", C.c_void_p), ("period", C.c_double),
         ("dtype", C.c_int), ("data", C.c_void_p), ("deg_m", C.c_double),
+        ("interp", C.c_int), ("ntracers", C.c_int), ("tracer", C.c_void_p * 2),
+        ("tracer_interp", C.c_int * 2),
     ]
 
 
 class _Kernel(C.Structure):
     _fields_ = [
         ("scheme", C.c_int), ("behaviours", C.c_uint), ("kh", C.c_double),
-        ("w_sink", C.c_double), ("seed", C.c_uint64),
+        ("w_sink", C.c_double), ("seed", C.c_uint64), ("dwell_depth", C.c_double),
+        ("max_age", C.c_double),
     ]
 
 
@@ -79,7 +83,10 @@ def lib():
             L.or_normal_pair.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, dp, dp]
             L.or_normal_pair.restype = None
             L.or_run.argtypes = [C.POINTER(_FieldSet), C.POINTER(_Kernel), C.c_int64] + \
-                [C.c_void_p] * 7 + [C.c_double, C.c_double, C.c_double, C.c_int]
+                [C.c_void_p] * 9 + [C.c_double, C.c_double, C.c_double, C.c_int]
+            L.or_sample_tracer.argtypes = [C.POINTER(_FieldSet), C.c_int, C.c_double,
+                                           C.c_double, C.c_double, C.c_double, dp]
+            L.or_sample_tracer.restype = C.c_int
             L.or_run.restype = C.c_int64
             L.or_quantise.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_void_p]
             L.or_quantise.restype = C.c_float
@@ -101,7 +108,10 @@ class Field:
     """
 
     def __init__(self, lon, lat, depth, times, data, mesh=FLAT, periodic_lon=False,
-                 period=0.0, deg_m=DEG_M):
+                 period=0.0, deg_m=DEG_M, interp=LINEAR, tracers=(), tracer_interp=()):
+        """``tracers``: up to two scalar fields (nt, nz, ny, nx) of the data's
+        dtype, sampled by the SAMPLE behaviour; ``interp`` and
+        ``tracer_interp``: LINEAR or NEAREST in space (time is linear)."""
         self.lon = np.ascontiguousarray(lon, dtype=np.float64)
         self.lat = np.ascontiguousarray(lat, dtype=np.float64)
         self.depth = np.ascontiguousarray(np.atleast_1d(depth), dtype=np.float64)
@@ -112,24 +122,36 @@ class Field:
         nt, nf, nz, ny, nx = self.data.shape
         assert (nt, nz, ny, nx) == (len(self.times), len(self.depth), len(self.lat), len(self.lon))
         assert nf in (2, 3)
+        assert len(tracers) <= 2
+        self.tracers = [np.ascontiguousarray(a, dtype=self.data.dtype) for a in tracers]
+        for a in self.tracers:
+            assert a.shape == (nt, nz, ny, nx)
+        ti = list(tracer_interp) + [LINEAR] * (len(self.tracers) - len(tracer_interp))
         self.s = _FieldSet(nx, ny, nz, _ptr(self.lon), _ptr(self.lat), _ptr(self.depth),
                            int(mesh), int(bool(periodic_lon)), nf, nt, _ptr(self.times),
                            float(period), 0 if self.data.dtype == np.float64 else 1,
-                           _ptr(self.data), float(deg_m))
+                           _ptr(self.data), float(deg_m), int(interp), len(self.tracers),
+                           (C.c_void_p * 2)(*([_ptr(a) for a in self.tracers] +
+                                              [None] * (2 - len(self.tracers)))),
+                           (C.c_int * 2)(*(ti + [0] * (2 - len(ti)))))
 
 
 class Kernel:
-    def __init__(self, scheme=RK4, behaviours=0, kh=0.0, w_sink=0.0, seed=0):
-        self.k = _Kernel(int(scheme), int(behaviours), float(kh), float(w_sink), int(seed))
+    def __init__(self, scheme=RK4, behaviours=0, kh=0.0, w_sink=0.0, seed=0, dwell_depth=0.0,
+                 max_age=0.0):
+        self.k = _Kernel(int(scheme), int(behaviours), float(kh), float(w_sink), int(seed),
+                         float(dwell_depth), float(max_age))
 
 
 def run(field: Field, kernel: Kernel, lon, lat, depth, time, ids, step, status, dt,
-        t_stop, t_end=None, nthreads=None):
+        t_stop, t_end=None, nthreads=None, age=None, variables=None):
     """Advance particles in place (arrays: float64 x4, uint64, uint32, uint8).
 
     Every live particle steps while its time is before ``t_stop`` and before
     ``t_end`` (in the direction of dt); the last step is shortened to land on
-    ``t_end``.  Returns the number of particle-steps taken.
+    ``t_end``.  ``age`` (float64 [n]) and ``variables`` (float64 [ntracers, n])
+    are updated by the AGE and SAMPLE behaviours.  Returns the number of
+    particle-steps taken.
     """
     if t_end is None:
         t_end = t_stop
@@ -139,12 +161,25 @@ def run(field: Field, kernel: Kernel, lon, lat, depth, time, ids, step, status, 
                    (time, np.float64), (ids, np.uint64), (step, np.uint32), (status, np.uint8)):
         assert a.dtype == dt_ and a.flags.c_contiguous
     n = len(lon)
+    for a, shape in ((age, (n,)), (variables, (len(field.tracers), n))):
+        if a is not None:
+            assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == shape
     r = lib().or_run(C.byref(field.s), C.byref(kernel.k), n, _ptr(lon), _ptr(lat), _ptr(depth),
-                     _ptr(time), _ptr(ids), _ptr(step), _ptr(status), float(dt), float(t_stop),
-                     float(t_end), int(nthreads))
+                     _ptr(time), _ptr(ids), _ptr(step), _ptr(status),
+                     _ptr(age) if age is not None else None,
+                     _ptr(variables) if variables is not None else None, float(dt),
+                     float(t_stop), float(t_end), int(nthreads))
+    if r == -2:
+        raise ValueError("the SAMPLE behaviour needs the variables array")
     if r < 0:
         raise ValueError("time span outside the field's time range")
     return int(r)
+
+
+def sample_tracer(field: Field, tr, t, lon, lat, depth=0.0):
+    out = C.c_double()
+    r = lib().or_sample_tracer(C.byref(field.s), int(tr), t, lon, lat, depth, C.byref(out))
+    return r, out.value
 
 
 def sample(field: Field, t, lon, lat, depth=0.0):

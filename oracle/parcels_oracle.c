@@ -28,7 +28,21 @@
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the seed,
  *     counter (id lo, id hi, step, stream), then Box-Muller;
  *   - a step whose stage or final position leaves the domain is not applied and
- *     the particle is deleted (status != 0).
+ *     the particle is deleted (status != 0);
+ *   - nearest-neighbour interpolation (Sect. 2.3) picks, on each axis, the
+ *     node nearest to the position, the lower one on a tie; time stays linear;
+ *   - the worked example of Sect. 3 (sinking phase, age with a maximum, sampled
+ *     temperature, constants carried by the FieldSet) as three behaviours that
+ *     run after advection, Brownian motion and sinking, in this order:
+ *       settle: while the depth differs from the dwelling depth at the step's
+ *         start, the depth moves by w_sink * h and stops at the dwelling depth
+ *         when it reaches or passes it; a particle that starts the step at the
+ *         dwelling depth holds it (vertical advection and sinking discarded);
+ *       age: age += |h| for every step (with settle: every step that starts at
+ *         the dwelling depth); once age >= max_age the particle is deleted with
+ *         status 4 and keeps the step's result;
+ *       sample: each scalar field is interpolated at the step's new position
+ *         and time into the particle's variable (NaN where the field is NaN).
  * Philox4x32-10 is pinned by the generator's published known-answer vectors;
  * the word-to-uniform mapping of Box-Muller by a value computed by hand from
  * one of them.
@@ -56,6 +70,10 @@ typedef struct {
     int dtype;                    /* 0: double data, 1: float data             */
     const void *data;             /* [nt][nfields][nz][ny][nx], lon fastest    */
     double deg_m;                 /* metres per degree on the sphere           */
+    int interp;                   /* velocities: 0 linear, 1 nearest node      */
+    int ntracers;                 /* scalar fields sampled into variables      */
+    const void *tracer[2];        /* each [nt][nz][ny][nx], dtype as data      */
+    int tracer_interp[2];         /* 0 linear, 1 nearest node                  */
 } or_fieldset;
 
 typedef struct {
@@ -64,10 +82,12 @@ typedef struct {
     double kh;                    /* m^2/s                                     */
     double w_sink;                /* m/s, positive downward                    */
     uint64_t seed;
+    double dwell_depth;           /* settle: depth where the vertical move ends */
+    double max_age;               /* age: deletion age in seconds              */
 } or_kernel;
 
-enum { OR_ALIVE = 0, OR_OOB_HORIZ = 1, OR_OOB_DEPTH = 2, OR_NAN = 3 };
-enum { OR_BROWNIAN = 1u, OR_SINK = 2u };
+enum { OR_ALIVE = 0, OR_OOB_HORIZ = 1, OR_OOB_DEPTH = 2, OR_NAN = 3, OR_DELETED = 4 };
+enum { OR_BROWNIAN = 1u, OR_SINK = 2u, OR_SETTLE = 4u, OR_AGE = 8u, OR_SAMPLE = 16u };
 
 /* ------------------------------------------------------------------------ */
 /* Cell search (Sect. 2.4: rectilinear axes).                                */
@@ -170,6 +190,20 @@ static double field_value(const or_fieldset *fs, int s, int f, int k, int j, int
     return (double)((const float *)fs->data)[idx];
 }
 
+static double tracer_value(const or_fieldset *fs, int tr, int s, int k, int j, int i)
+{
+    size_t idx = (((size_t)s * fs->nz + k) * fs->ny + j) * fs->nx + i;
+    if (fs->dtype == 0) return ((const double *)fs->tracer[tr])[idx];
+    return (double)((const float *)fs->tracer[tr])[idx];
+}
+
+/* Nearest node of a cell on one axis: the lower node unless the fraction is
+ * above one half (a tie goes to the lower node). */
+static int nearest_node(int lo, int hi, double frac)
+{
+    return frac <= 0.5 ? lo : hi;
+}
+
 /* Bilinear weights applied as (w00 f00 + w10 f10) + (w11 f11 + w01 f01). */
 static double interp_2d(const or_fieldset *fs, int s, int f, int k,
                         int i0, int i1, int j0, int j1, double xi, double eta)
@@ -214,17 +248,67 @@ int or_sample(const or_fieldset *fs, double t, double lon, double lat, double de
     int s0, s1;
     double tau;
     if (or_time_interval(fs, t, &s0, &s1, &tau)) return -1;
+    int in = nearest_node(i0, i1, xi), jn = nearest_node(j0, j1, eta);
+    int kn = nearest_node(k0, k1, zeta);
     for (int f = 0; f < fs->nfields; ++f) {
-        double a = interp_space(fs, s0, f, i0, i1, j0, j1, k0, k1, xi, eta, zeta);
-        double v = a;
+        double a, v;
+        if (fs->interp == 1) a = field_value(fs, s0, f, kn, jn, in);
+        else a = interp_space(fs, s0, f, i0, i1, j0, j1, k0, k1, xi, eta, zeta);
+        v = a;
         if (fs->nt > 1) {
-            double b = interp_space(fs, s1, f, i0, i1, j0, j1, k0, k1, xi, eta, zeta);
+            double b;
+            if (fs->interp == 1) b = field_value(fs, s1, f, kn, jn, in);
+            else b = interp_space(fs, s1, f, i0, i1, j0, j1, k0, k1, xi, eta, zeta);
             v = a + (b - a) * tau;
         }
         if (!(v == v)) return OR_NAN;
         out[f] = v;
     }
     if (fs->nfields == 2) out[2] = 0.0;
+    return OR_ALIVE;
+}
+
+/* Sample scalar field tr (Sect. 3: a field sampled by a kernel) at a
+ * position and time, linearly or at the nearest node in space as the field
+ * says, linearly in time.  Returns 0 and the value (NaN where the field is
+ * NaN), an OR_OOB_* status, or -1 for a time outside a non-periodic range. */
+int or_sample_tracer(const or_fieldset *fs, int tr, double t, double lon, double lat,
+                     double depth, double *out)
+{
+    int i0, i1, j0, j1, k0 = 0, k1 = 0;
+    double xi, eta, zeta = 0.0;
+    if (or_locate_lon(fs->lon, fs->nx, fs->periodic_lon, lon, &i0, &i1, &xi)) return OR_OOB_HORIZ;
+    if (or_locate(fs->lat, fs->ny, lat, &j0, &eta)) return OR_OOB_HORIZ;
+    j1 = (fs->ny == 1) ? j0 : j0 + 1;
+    if (fs->nz > 1) {
+        if (or_locate(fs->depth, fs->nz, depth, &k0, &zeta)) return OR_OOB_DEPTH;
+        k1 = k0 + 1;
+    }
+    int s0, s1;
+    double tau;
+    if (or_time_interval(fs, t, &s0, &s1, &tau)) return -1;
+    double val[2];
+    for (int q = 0; q < (fs->nt > 1 ? 2 : 1); ++q) {
+        int s = q == 0 ? s0 : s1;
+        if (fs->tracer_interp[tr] == 1) {
+            val[q] = tracer_value(fs, tr, s, nearest_node(k0, k1, zeta), nearest_node(j0, j1, eta),
+                                  nearest_node(i0, i1, xi));
+        } else {
+            double w00 = (1.0 - xi) * (1.0 - eta);
+            double w10 = xi * (1.0 - eta);
+            double w11 = xi * eta;
+            double w01 = (1.0 - xi) * eta;
+            double a = (w00 * tracer_value(fs, tr, s, k0, j0, i0) + w10 * tracer_value(fs, tr, s, k0, j0, i1)) +
+                       (w11 * tracer_value(fs, tr, s, k0, j1, i1) + w01 * tracer_value(fs, tr, s, k0, j1, i0));
+            if (fs->nz > 1) {
+                double b = (w00 * tracer_value(fs, tr, s, k1, j0, i0) + w10 * tracer_value(fs, tr, s, k1, j0, i1)) +
+                           (w11 * tracer_value(fs, tr, s, k1, j1, i1) + w01 * tracer_value(fs, tr, s, k1, j1, i0));
+                a = (1.0 - zeta) * a + zeta * b;
+            }
+            val[q] = a;
+        }
+    }
+    *out = fs->nt > 1 ? val[0] + (val[1] - val[0]) * tau : val[0];
     return OR_ALIVE;
 }
 
@@ -300,9 +384,12 @@ static int out_of_domain(const or_fieldset *fs, double lon, double lat, double d
 }
 
 /* Advance one particle by h seconds.  On success the new state is written and
- * 0 returned; otherwise the state is left untouched and the status returned. */
+ * 0 returned (OR_DELETED when the age behaviour deleted it, with the new state
+ * written); otherwise the state is left untouched and the status returned.
+ * age and vars (stride vstride between variables) are written on success. */
 static int step_one(const or_fieldset *fs, const or_kernel *kn, double *plon, double *plat,
-                    double *pdep, double t, double h, uint64_t id, uint32_t step)
+                    double *pdep, double t, double h, uint64_t id, uint32_t step,
+                    double *page, double *pvars, int64_t vstride)
 {
     double lon = *plon, lat = *plat, dep = *pdep;
     double k1[3], k2[3], k3[3], k4[3];
@@ -340,10 +427,33 @@ static int step_one(const or_fieldset *fs, const or_kernel *kn, double *plon, do
         nlat = nlat + dy;
     }
     if (kn->behaviours & OR_SINK) ndep = ndep + kn->w_sink * h;
+    int dwelling = 0;                    /* the step starts at the dwelling depth */
+    if (kn->behaviours & OR_SETTLE) {
+        if (dep == kn->dwell_depth) {
+            dwelling = 1;
+            ndep = kn->dwell_depth;
+        } else {
+            double moved = ndep + kn->w_sink * h;
+            if ((dep - kn->dwell_depth) * (moved - kn->dwell_depth) <= 0.0) moved = kn->dwell_depth;
+            ndep = moved;
+        }
+    }
     if (fs->periodic_lon) nlon = or_wrap_lon(nlon, fs->lon[0]);
     if ((r = out_of_domain(fs, nlon, nlat, ndep))) return r;
     *plon = nlon; *plat = nlat; *pdep = ndep;
-    return OR_ALIVE;
+    int status = OR_ALIVE;
+    if (kn->behaviours & OR_AGE) {
+        if (!(kn->behaviours & OR_SETTLE) || dwelling) *page = *page + fabs(h);
+        if (*page >= kn->max_age) status = OR_DELETED;
+    }
+    if (kn->behaviours & OR_SAMPLE) {
+        for (int q = 0; q < fs->ntracers; ++q) {
+            double v;
+            if (or_sample_tracer(fs, q, t + h, nlon, nlat, ndep, &v) == OR_ALIVE)
+                pvars[q * vstride] = v;
+        }
+    }
+    return status;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -357,6 +467,8 @@ typedef struct {
     const uint64_t *id;
     uint32_t *step;
     uint8_t *status;
+    double *age, *vars;            /* age[n], vars[ntracers][n]; may be NULL */
+    int64_t n;
     double dt, t_stop, t_end;
     int64_t begin, end;
     int64_t steps_done;
@@ -375,8 +487,17 @@ static void *run_range(void *arg)
         while (sgn * (jb->t_stop - t) > 0.0 && sgn * (jb->t_end - t) > 0.0) {
             double h = jb->dt;
             if (sgn * (jb->t_end - t) < sgn * h) h = jb->t_end - t;
+            double age_dummy = 0.0;
             int r = step_one(jb->fs, jb->kn, &jb->lon[p], &jb->lat[p], &jb->depth[p],
-                             t, h, jb->id[p], jb->step[p]);
+                             t, h, jb->id[p], jb->step[p], jb->age ? &jb->age[p] : &age_dummy,
+                             jb->vars ? &jb->vars[p] : NULL, jb->n);
+            if (r == OR_DELETED) {          /* the step was taken, then the age deleted it */
+                t = t + h;
+                jb->step[p] += 1u;
+                ++done;
+                jb->status[p] = (uint8_t)r;
+                break;
+            }
             if (r) { jb->status[p] = (uint8_t)r; break; }
             t = t + h;
             jb->step[p] += 1u;
@@ -392,10 +513,11 @@ static void *run_range(void *arg)
  * the time span leaves a non-periodic field's time range. */
 int64_t or_run(const or_fieldset *fs, const or_kernel *kn, int64_t n, double *lon,
                double *lat, double *depth, double *time, const uint64_t *id,
-               uint32_t *step, uint8_t *status, double dt, double t_stop, double t_end,
-               int nthreads)
+               uint32_t *step, uint8_t *status, double *age, double *vars, double dt,
+               double t_stop, double t_end, int nthreads)
 {
     if (n <= 0) return 0;
+    if ((kn->behaviours & OR_SAMPLE) && fs->ntracers > 0 && !vars) return -2;
     if (fs->nt > 1 && fs->period <= 0.0) {
         for (int64_t p = 0; p < n; ++p) {
             if (status[p] != OR_ALIVE) continue;
@@ -413,6 +535,7 @@ int64_t or_run(const or_fieldset *fs, const or_kernel *kn, int64_t n, double *lo
         jb->fs = fs; jb->kn = kn;
         jb->lon = lon; jb->lat = lat; jb->depth = depth; jb->time = time;
         jb->id = id; jb->step = step; jb->status = status;
+        jb->age = age; jb->vars = vars; jb->n = n;
         jb->dt = dt; jb->t_stop = t_stop; jb->t_end = t_end;
         jb->begin = (int64_t)w * chunk;
         jb->end = jb->begin + chunk < n ? jb->begin + chunk : n;
