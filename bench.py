@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--resort-steps", type=int, default=288)
     ap.add_argument("--chunk-steps", type=int, default=288)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-ring", type=int, default=4,
+                    help="snapshot ring slots of the end-to-end leg (4: two in use + the next)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="3d", choices=["3d", "precision", "batch", "surrogate"],
@@ -112,20 +114,31 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(particle_steps_per_launch):
-    """DRAM bytes per launch of the advection kernel: the per-particle-step
-    DRAM bytes of a committed ncu capture (taken on the current kernel source,
-    else None) times the particle-steps of one launch."""
+def captured_traffic():
+    """Per-particle-step DRAM and L2 bytes of the advection kernel from a
+    committed ncu capture, or None when the capture was taken on another
+    version of the kernel source."""
     p = os.path.join(ROOT, "profiles", "advect_f32_3d_traffic.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p))
         if d.get("kernel_hash") == kernel_hash():
-            return float(d["dram_bytes_per_particle_step"]) * particle_steps_per_launch
+            return d
     except Exception:
         pass
     return None
+
+
+def l2_read_peak(lib):
+    """Measured L2 read bandwidth (GB/s) of this GPU: the library's probe, a
+    32 MiB L2-resident buffer read with coalesced 16-byte loads that bypass
+    L1, best of 10 launches."""
+    import ctypes as C
+    g = C.c_double()
+    if lib.pg_measure_l2_read(32 << 20, 10, C.byref(g), None) != 0:
+        return None
+    return g.value
 
 
 class ClockSampler:
@@ -298,10 +311,15 @@ def main():
     elapsed_ms, total_all = reduce_over_ranks(elapsed_ms, total_steps, dev)
     value = total_all / (elapsed_ms / 1e3)
 
-    # end-to-end through the C ABI from host buffers
-    e2e = None
+    # the field streamed from pinned host memory (two snapshots in use plus
+    # the next one uploading): device-timed with particles on the device, and
+    # end to end through the C ABI from host buffers
+    e2e, streamed = None, None
     if not args.no_e2e and host_field is not None:
-        e2e = e2e_leg(pg, gf, torch, host_field, lon, lat, dep, kern, runtime, args)
+        streamed = {f"ring{r}": streamed_leg(pg, gf, torch, host_field, lon, lat, dep, kern,
+                                             runtime, args, r, False) for r in (4, 10)}
+        e2e = streamed_leg(pg, gf, torch, host_field, lon, lat, dep, kern, runtime, args,
+                           args.e2e_ring, True)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and host_field is not None:
@@ -309,16 +327,32 @@ def main():
                                     args.cpu_seconds)
 
     hbm_peak, peak_kind = measured_peaks()
+    l2_peak = l2_read_peak(lib) if rank == 0 else None
     avg_launch_s = (kern_ms / 1e3) / max(kern_launches, 1)
     steps_per_launch = total_steps / max(kern_launches, 1)
+    kernel_rate = steps_per_launch / avg_launch_s          # particle-steps/s inside the kernel
     # The kernel keeps each cell's corner values in registers across stages
     # and steps, so it is bound by instruction issue, not by memory: report it
-    # against the FP32 FMA peak (152 SMs x 128 lanes x 2 FLOP x SM clock).
+    # against the FP32 FMA peak (SMs x 128 lanes x 2 FLOP x SM clock).
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    achieved = ALGO_FLOPS_PER_STEP * steps_per_launch / avg_launch_s / 1e12
-    gather_gbs = ALGO_BYTES_PER_STEP * steps_per_launch / avg_launch_s / 1e9
-    traffic = traffic_per_launch(steps_per_launch)
+    fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = ALGO_FLOPS_PER_STEP * kernel_rate / 1e12
+    cap = captured_traffic()
+    traffic = cap["dram_bytes_per_particle_step"] * steps_per_launch if cap else None
+    l2_view = hbm_view = None
+    if cap and cap.get("l2_bytes_per_particle_step") and l2_peak:
+        b = cap["l2_bytes_per_particle_step"]
+        l2_view = {"bytes_per_particle_step": b, "achieved_GBps": b * kernel_rate / 1e9,
+                   "peak_GBps": l2_peak, "frac": b * kernel_rate / 1e9 / l2_peak,
+                   "peak_source": "measured live: 32 MiB L2-resident buffer, coalesced "
+                                  "ld.global.cg, best of 10 (pg_measure_l2_read)"}
+    if cap:
+        b = cap["dram_bytes_per_particle_step"]
+        hbm_view = {"bytes_per_particle_step": b, "achieved_GBps": b * kernel_rate / 1e9,
+                    "peak_GBps": hbm_peak, "frac": b * kernel_rate / 1e9 / hbm_peak,
+                    "peak_source": peak_kind}
+    gather_gbs = ALGO_BYTES_PER_STEP * kernel_rate / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
@@ -332,16 +366,25 @@ def main():
                    "l2": "inputs larger than L2 (24.9 GB field, 10M-particle state)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
+                     "alu_frac": achieved / fp32_peak,
+                     "l2_frac": l2_view["frac"] if l2_view else None,
+                     "hbm_frac": hbm_view["frac"] if hbm_view else None,
+                     "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
                      "kernel": "advect_plain_kernel<float, float, 3, true, GEO_SPH_PER>",
                      "algorithmic_flops_per_particle_step": ALGO_FLOPS_PER_STEP,
                      "avg_launch_ms": avg_launch_s * 1e3, "launches": kern_launches,
+                     "l2": l2_view, "hbm": hbm_view,
+                     "traffic_capture": cap.get("captured") if cap else None,
                      "gather_view": {"algorithmic_bytes_per_particle_step": ALGO_BYTES_PER_STEP,
-                                     "effective_GBps": gather_gbs, "hbm_peak_GBps": hbm_peak,
-                                     "hbm_peak_source": peak_kind,
-                                     "dram_bytes_per_launch": traffic}},
+                                     "effective_GBps": gather_gbs,
+                                     "meaning": "the corner values the definition gathers at "
+                                                "every stage, 768 B + 42 B of state; the "
+                                                "kernel keeps a cell's corners in registers, "
+                                                "so its L2 and DRAM traffic (l2, hbm) is far "
+                                                "below this"}},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "streamed": streamed,
         "gpu_launches": int(c1.value - c0.value),
         "clocks": clk,
         "particle_steps": total_all,
@@ -352,44 +395,76 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def e2e_leg(pg, gf, torch, host_field, lon, lat, dep, kern, runtime, args):
-    """Same workload from host memory: snapshots streamed H2D inside execute,
-    particles uploaded and final state read back, all inside the timed region."""
+def streamed_leg(pg, gf, torch, host_field, lon, lat, dep, kern, runtime, args, ring,
+                 from_host):
+    """The workload with its snapshots streamed from pinned host memory
+    through a ring of `ring` device slots (4: two snapshots in use by a
+    launch, one for steps that reach past it, the next uploading; launches
+    end at the next snapshot time).  from_host: particles uploaded from
+    pinned FP64 host arrays and the final state read back into them, all
+    inside the timed region (the end-to-end number); otherwise particles
+    start on the device and only the execute is timed (CUDA events).
+    Returns the best of two runs with its breakdown."""
     import ctypes as C
     n = len(lon)
     fs = pg.FieldSet(gf.lon, gf.lat, gf.depth, mesh="spherical", periodic_lon=True,
                      nfields=gf.nfields, storage="f32")
     fs.set_times(gf.times, gf.period)
+    fs.set_ring(ring)
     fs.stream([host_field[s] for s in range(len(gf.times))])
-    hl = torch.from_numpy(lon).pin_memory()
-    ha = torch.from_numpy(lat).pin_memory()
-    hd = torch.from_numpy(dep).pin_memory()
-    out = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in ("lon", "lat", "depth")}
-    ost = torch.empty(n, dtype=torch.uint8).pin_memory()
+    if from_host:
+        src = [torch.from_numpy(np.asarray(a, np.float64)).pin_memory() for a in (lon, lat, dep)]
+        out = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in ("lon", "lat", "depth")}
+        ost = torch.empty(n, dtype=torch.uint8).pin_memory()
+    else:
+        src = [torch.from_numpy(a).cuda() for a in (lon, lat, dep)]
     lib = pg.load()
     best = None
-    h2d_field = 0
     for rep in range(2):
         lib.pg_fieldset_stats(fs.h, 1, None, None)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ps = pg.ParticleSet(fs, hl, ha, hd, pos="f32", seed=0)
+        w0 = time.perf_counter()
+        ev[0].record()
+        ps = pg.ParticleSet(fs, src[0], src[1], src[2], pos="f32", seed=0)
+        ev[1].record()
         ps.set_tune(args.block, args.resort_steps, args.chunk_steps)
+        lib.pg_pset_kernel_timing(ps.h, 1, None, None)
         steps = ps.execute(kern, runtime, 1800.0)
-        ps.get_into(lon=out["lon"], lat=out["lat"], depth=out["depth"], status=ost)
+        ev[2].record()
+        if from_host:
+            ps.get_into(lon=out["lon"], lat=out["lat"], depth=out["depth"], status=ost)
+        ev[3].record()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        wall = time.perf_counter() - w0
+        kms, kl = C.c_double(), C.c_int64()
+        lib.pg_pset_kernel_timing(ps.h, -1, C.byref(kms), C.byref(kl))
         ps.destroy()
-        ub = C.c_int64()
-        lib.pg_fieldset_stats(fs.h, 1, None, C.byref(ub))
-        if best is None or dt < best[0]:
-            best = (dt, steps)
-            h2d_field = ub.value
-    h2d = h2d_field + n * 3 * 4          # snapshot uploads + float32 positions
-    d2h = n * (3 * 8 + 1)
+        ups, ub = C.c_int64(), C.c_int64()
+        lib.pg_fieldset_stats(fs.h, 1, C.byref(ups), C.byref(ub))
+        ex_ms = ev[1].elapsed_time(ev[2])
+        rec = {"wall_s": wall, "steps": steps,
+               "particles_h2d_ms": ev[0].elapsed_time(ev[1]), "execute_ms": ex_ms,
+               "advection_kernels_ms": kms.value, "launches": kl.value,
+               "execute_other_ms": ex_ms - kms.value,
+               "results_d2h_ms": ev[2].elapsed_time(ev[3]),
+               "snapshot_uploads": ups.value, "snapshot_h2d_bytes": ub.value}
+        key = wall if from_host else ex_ms
+        if best is None or key < best[0]:
+            best = (key, rec)
     fs.destroy()
-    return {"value": best[1] / best[0], "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "seconds": best[0]}
+    rec = best[1]
+    rec["ring"] = ring
+    rec["note"] = ("execute_other_ms = execute minus its advection kernels: re-sorts, waits "
+                   "for snapshot uploads, launch gaps")
+    if from_host:
+        h2d = rec["snapshot_h2d_bytes"] + n * 3 * 8        # snapshots + FP64 positions
+        d2h = n * (3 * 8 + 1)
+        return {"value": rec["steps"] / rec["wall_s"], "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "seconds": rec["wall_s"], "breakdown": rec}
+    rec["value"] = rec["steps"] / (rec["execute_ms"] / 1e3)
+    rec["unit"] = UNIT
+    return rec
 
 
 def reference_arm(args, rank, world):

@@ -85,9 +85,36 @@ typedef int pg_status;
 #define PG_EULER 0
 #define PG_RK4 1
 
-/* Behaviour bits, applied after advection in this order. */
+/* Behaviour bits, applied after advection in this order.  SETTLE, AGE and
+ * SAMPLE are the custom kernels of the paper's worked example (Sect. 3; the
+ * backward run of virtual foraminifera): their parameters are constants of
+ * the field set (pg_fieldset_add_constant).
+ *   BROWNIAN: each horizontal coordinate += sqrt(2 Kh |dt|) N(0, 1).
+ *   SINK:     depth += w_sink dt.
+ *   SETTLE:   while the depth at the start of a step differs from the
+ *             constant "dwelling_depth", depth += w_sink dt, stopping at the
+ *             dwelling depth when it reaches or passes it; a step that starts
+ *             at the dwelling depth holds it (vertical advection discarded).
+ *   AGE:      age += |dt| per step (with SETTLE: per step that starts at the
+ *             dwelling depth); a particle whose age reaches the constant
+ *             "max_age" is deleted with status PG_DELETED after its step.
+ *   SAMPLE:   every scalar field of the field set (pg_fieldset_add_scalar)
+ *             is interpolated at the particle's position and time after the
+ *             step into the particle's variable (pg_pset_get_variables).
+ * SETTLE, AGE, SAMPLE and nearest-neighbour interpolation need lon/lat/depth
+ * positions (PG_POS_F64, or PG_POS_F32 on PG_F32 storage) and run outside
+ * pg_execute_batch. */
 #define PG_BROWNIAN 1u
 #define PG_SINK 2u
+#define PG_SETTLE 4u
+#define PG_AGE 8u
+#define PG_SAMPLE 16u
+
+/* Spatial interpolation of a field (Sect. 2.3): linear (bi/trilinear), or
+ * the nearest node on each axis (the lower node on a tie).  Time is always
+ * linear. */
+#define PG_LINEAR 0
+#define PG_NEAREST 1
 
 /* Particle status (one byte per particle).  Any non-zero status means the
  * particle was deleted; its position and time are those before the step
@@ -96,6 +123,7 @@ typedef int pg_status;
 #define PG_OOB_HORIZ 1 /* a stage or final position left the lon/lat range */
 #define PG_OOB_DEPTH 2 /* a stage or final position left the depth range   */
 #define PG_NAN 3       /* a sampled velocity was NaN                        */
+#define PG_DELETED 4   /* deleted by the AGE behaviour (state after its step) */
 
 typedef struct pg_fieldset pg_fieldset;
 typedef struct pg_pset pg_pset;
@@ -123,13 +151,34 @@ typedef struct {
  * with PG_ERR_CALLBACK. */
 typedef int (*pg_snapshot_cb)(void *user, int s, void *dst, size_t bytes);
 
-/* Output hook, called at every output time (the ParticleFile of Sect. 3).
- * Arrays are host memory valid during the call only, n entries in the
- * library's internal order (use `id` to match particles).  Non-zero return
- * aborts the execute with PG_ERR_CALLBACK. */
+/* Output hook, called at every output time (the ParticleFile of Sect. 3)
+ * with every particle of the set.  Arrays are host memory (pinned, owned by
+ * the library) valid during the call only, n entries in the library's
+ * internal order (use `id` to match particles).  The hook for output time t
+ * runs on the calling thread while the GPU already advances the particles
+ * past t (at the next output time or at the end of the execute), so the copy
+ * and the hook overlap the computation.  Non-zero return aborts the execute
+ * with PG_ERR_CALLBACK. */
 typedef int (*pg_output_cb)(void *user, double time, int64_t n, const uint64_t *id,
                             const double *lon, const double *lat, const double *depth,
                             const uint8_t *status);
+
+/* One output record set (pg_execute_records): n rows, library order, host
+ * memory valid during the hook only.  Row i: particle id[i] at lon[i],
+ * lat[i], depth[i] (FP64), status[i], age[i] and its sampled variables
+ * vars[j * var_stride + i], j < nvar. */
+typedef struct {
+    double time;
+    int64_t n;
+    int nvar;
+    int64_t var_stride;
+    const uint64_t *id;
+    const double *lon, *lat, *depth;
+    const uint8_t *status;
+    const double *age;
+    const double *vars;
+} pg_record;
+typedef int (*pg_record_cb)(void *user, const pg_record *rec);
 
 /* ---------------------------------------------------------------- errors */
 
@@ -162,13 +211,22 @@ PG_API pg_status pg_fieldset_load_snapshot(pg_fieldset *fs, int s, const void *d
                                     void *stream);
 
 /* Stream snapshots instead of keeping them all resident: the library keeps
- * four device slots and, during pg_execute, uploads the next snapshot on its
- * own side stream while the current ones are in use.  Source: either `ptrs`
+ * a ring of device slots (four unless pg_fieldset_set_ring says otherwise)
+ * and, during pg_execute, uploads the next snapshot on its own side stream
+ * while the current ones are in use.  Source: either `ptrs`
  * (nt host or device pointers, each valid for the lifetime of the field
  * set), or `cb` (called with a pinned host buffer to fill).  Exactly one of
  * ptrs / cb must be non-NULL. */
 PG_API pg_status pg_fieldset_stream(pg_fieldset *fs, const void *const *ptrs, pg_snapshot_cb cb,
                              void *user, int src_dtype);
+
+/* Size of the streamed-snapshot ring, before pg_fieldset_stream: `slots`
+ * device slots of one snapshot each, 4 (default: two snapshots in use by a
+ * launch, the third for steps that reach past its end, the next one
+ * uploading; the three time slices of Sect. 3 plus the prefetch) to 64.  A
+ * launch spans at most slots - 4 snapshot times after the next one, so larger
+ * rings allow longer launches at slots x (snapshot bytes) of device memory. */
+PG_API pg_status pg_fieldset_set_ring(pg_fieldset *fs, int slots);
 
 /* Device bytes held by the field set's snapshot storage. */
 PG_API pg_status pg_fieldset_device_bytes(const pg_fieldset *fs, size_t *bytes);
@@ -176,6 +234,35 @@ PG_API pg_status pg_fieldset_device_bytes(const pg_fieldset *fs, size_t *bytes);
 /* FP32 scale of (field f, snapshot s) for F16S/BF16S storage (1.0 otherwise).
  * Resident storage only. */
 PG_API pg_status pg_fieldset_get_scale(const pg_fieldset *fs, int s, int f, float *scale);
+
+/* Named constants of the field set (Sect. 3: the worked example adds three
+ * global constants to its FieldSet for its custom kernels).  The behaviours
+ * read "Kh" (m^2/s, BROWNIAN when the kernel's kh is NaN), "w_sink" (m/s,
+ * SINK and SETTLE when the kernel's w_sink is NaN), "dwelling_depth" (m,
+ * SETTLE) and "max_age" (s, AGE) at execute time; other names are kept for
+ * the caller.  `name` is copied; values must be finite (PG_ERR_ARG).  Adding
+ * a name again replaces its value.  get returns PG_ERR_ARG for an unknown
+ * name. */
+PG_API pg_status pg_fieldset_add_constant(pg_fieldset *fs, const char *name, double value);
+PG_API pg_status pg_fieldset_get_constant(const pg_fieldset *fs, const char *name, double *value);
+
+/* Spatial interpolation of the velocity fields: PG_LINEAR (default) or
+ * PG_NEAREST (Sect. 2.3). */
+PG_API pg_status pg_fieldset_set_interp(pg_fieldset *fs, int method);
+
+/* Scalar fields on the same grid and snapshot times as the velocities (the
+ * temperature field the worked example samples, Sect. 3), at most two per
+ * field set, interpolated by `method` (PG_LINEAR / PG_NEAREST) in space and
+ * linearly in time.  add: after pg_fieldset_set_times and before the particle
+ * sets that sample it are created; *index (may be NULL) receives its number.
+ * load: snapshot s of scalar field `index`, [nz][ny][nx] lon fastest, host or
+ * device, src_dtype PG_F64 or PG_F32; stored in FP64 for PG_F64 field
+ * storage and in FP32 otherwise, resident in device memory the library owns
+ * (field sets whose velocities are streamed cannot be sampled).
+ * pg_fieldset_set_times drops loaded scalar snapshots. */
+PG_API pg_status pg_fieldset_add_scalar(pg_fieldset *fs, const char *name, int method, int *index);
+PG_API pg_status pg_fieldset_load_scalar(pg_fieldset *fs, int index, int s, const void *data,
+                                         int src_dtype, void *stream);
 
 PG_API pg_status pg_fieldset_destroy(pg_fieldset *fs);
 
@@ -185,7 +272,8 @@ PG_API pg_status pg_fieldset_destroy(pg_fieldset *fs);
  * kh: Brownian diffusivity in m^2/s (sigma per step sqrt(2 kh |dt|) metres,
  * normal variates from Philox4x32-10 keyed by the particle set's seed and
  * counted by (particle id, particle step)); w_sink: sinking speed in m/s
- * (depth += w_sink * dt). */
+ * (depth += w_sink * dt).  Either may be NaN: the field set's constant "Kh"
+ * or "w_sink" is then used at execute time (PG_ERR_STATE if it is absent). */
 PG_API pg_status pg_kernel_create(int scheme, unsigned behaviours, double kh, double w_sink,
                            pg_kernel **out);
 PG_API pg_status pg_kernel_destroy(pg_kernel *k);
@@ -208,15 +296,30 @@ PG_API pg_status pg_pset_add(pg_pset *ps, int64_t n, const double *lon, const do
                       const double *depth, const double *time, double t0, const uint64_t *ids,
                       uint64_t id_base);
 
-/* Number of particles (alive and deleted) and of alive particles. */
+/* Number of particles (alive and deleted) and of alive particles (the
+ * ParticleSet of Sect. 2.1, whose particles deletion removes from the
+ * computation, Sect. 3).  Either pointer may be NULL. */
 PG_API pg_status pg_pset_size(const pg_pset *ps, int64_t *n, int64_t *n_alive);
 
-/* Copy the particle state out (library order).  Any pointer may be NULL.
- * Host or device destinations of n entries each. */
+/* Copy the particle state out (the particle variables of Sect. 2.1: lon,
+ * lat, depth, time, plus id, step count and status), library order.  Any
+ * pointer may be NULL.  Host or device destinations of n entries each,
+ * positions widened to FP64. */
 PG_API pg_status pg_pset_get(const pg_pset *ps, double *lon, double *lat, double *depth, double *time,
                       uint64_t *ids, uint32_t *steps, uint8_t *status, void *stream);
 
-/* Tuning (block size, re-sort interval, steps per launch). */
+/* Particle variables (the extra Variables of the worked example's particle
+ * class, Sect. 3): age[n] in seconds (0 at creation) and, for the sample
+ * behaviour, vars[nvar * n] with variable j of particle i at vars[j * n + i]
+ * (NaN until a step has sampled it); nvar is the number of scalar fields the
+ * field set had when the particle set was created.  Library order, as
+ * pg_pset_get; host or device destinations; either may be NULL. */
+PG_API pg_status pg_pset_get_variables(const pg_pset *ps, double *age, double *vars, void *stream);
+
+/* Tuning of the time loop (Sect. 2.2: the execution loop; not a paper
+ * parameter): block size, re-sort interval and steps per launch.  Zero
+ * fields take defaults; PG_ERR_ARG for a block that is not a multiple of 32
+ * in [32, 1024] or negative intervals. */
 PG_API pg_status pg_pset_set_tune(pg_pset *ps, const pg_tune *tune);
 
 /* Advance every alive particle (the execute of Sect. 2.2 and 3): from the
@@ -229,6 +332,22 @@ PG_API pg_status pg_pset_set_tune(pg_pset *ps, const pg_tune *tune);
 PG_API pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
                      double output_dt, pg_output_cb out, void *user, void *stream,
                      int64_t *steps_done);
+
+/* pg_execute with trajectory output in the ParticleFile's form (Sect. 3):
+ * at every multiple of output_dt after the start and at the end, `rec` gets
+ * the rows of that output time.  indexed = 0: every particle.  indexed = 1:
+ * the 'indexed' format of Sect. 3, where particles are added and deleted
+ * during the run: only the particles alive at that time and those deleted
+ * since the previous output time (their last state and status), so each
+ * particle's records end with its deletion.  The rows are packed on the GPU
+ * and copied into a pinned two-slot ring on a side stream while the next
+ * launch runs; `rec` for output k is called when output k + 1 has been
+ * packed, and the last one before the call returns.  The ring holds 2 x
+ * (41 + 8 nvar) bytes per particle of device and pinned host memory, kept by
+ * the particle set for later executes. */
+PG_API pg_status pg_execute_records(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
+                                    double output_dt, int indexed, pg_record_cb rec, void *user,
+                                    void *stream, int64_t *steps_done);
 
 /* Batched form: advance many releases (the repeated releases of Sect. 3),
  * each a particle set with its own kernel, dt (> 0) and runtime, over one
@@ -362,8 +481,11 @@ PG_API pg_status pg_moments_f64_noalloc(const double *lon, const double *lat,
                                         double *out, void *stream);
 
 /* Checkpoint: write / read the complete particle state (positions, times,
- * ids, step counters, status, seed) to a file.  Restoring gives a set that
- * continues bit-identically. */
+ * ids, step counters, status, age and sampled variables, seed) to a file, so
+ * that a run executed in a loop of pg_execute calls (Sect. 3) can stop and
+ * resume.  Restoring gives a set that continues bit-identically; the field
+ * set must have as many scalar fields as the saved set had variables
+ * (PG_ERR_ARG otherwise, and for a file that is not a checkpoint). */
 PG_API pg_status pg_pset_save(const pg_pset *ps, const char *path);
 PG_API pg_status pg_pset_restore(pg_fieldset *fs, const char *path, pg_pset **out);
 
@@ -383,6 +505,15 @@ PG_API pg_status pg_pset_kernel_timing(pg_pset *ps, int enable, double *total_ms
  * reading). */
 PG_API pg_status pg_fieldset_stats(pg_fieldset *fs, int reset, int64_t *uploads,
                                    int64_t *h2d_bytes);
+
+/* Measured read bandwidth of the L2 cache in GB/s (the bound of a gather
+ * that hits in L2; the paper names field sampling as the dominant cost,
+ * Sect. 2.3, 5.1): a device buffer of `bytes` (at least 1 MiB, a multiple of
+ * 16, at most half the L2) is filled, read once to warm the cache, then read
+ * 16 times per launch with coalesced 16-byte loads that bypass L1; the best
+ * of `reps` launches timed with CUDA events on `stream` goes to *gbs.  The
+ * buffer is allocated and freed by the call. */
+PG_API pg_status pg_measure_l2_read(size_t bytes, int reps, double *gbs, void *stream);
 
 /* Number of kernel launches the library has made in this process. */
 PG_API pg_status pg_launch_count(int64_t *count);

@@ -19,8 +19,9 @@ PG_FLAT, PG_SPHERICAL = 0, 1
 PG_F64, PG_F32, PG_F16S, PG_BF16S = 0, 1, 2, 3
 PG_POS_F64, PG_POS_F32, PG_POS_CELL = 0, 1, 2
 PG_EULER, PG_RK4 = 0, 1
-PG_BROWNIAN, PG_SINK = 1, 2
-PG_ALIVE, PG_OOB_HORIZ, PG_OOB_DEPTH, PG_NAN = 0, 1, 2, 3
+PG_BROWNIAN, PG_SINK, PG_SETTLE, PG_AGE, PG_SAMPLE = 1, 2, 4, 8, 16
+PG_LINEAR, PG_NEAREST = 0, 1
+PG_ALIVE, PG_OOB_HORIZ, PG_OOB_DEPTH, PG_NAN, PG_DELETED = 0, 1, 2, 3, 4
 
 ERROR_NAMES = {
     -1: "PG_ERR_ARG", -2: "PG_ERR_CUDA", -3: "PG_ERR_STATE", -4: "PG_ERR_TIME",
@@ -55,6 +56,15 @@ SNAPSHOT_CB = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_size_t)
 OUTPUT_CB = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_double, C.c_int64, C.c_void_p, C.c_void_p,
                         C.c_void_p, C.c_void_p, C.c_void_p)
 
+class Record(C.Structure):
+    _fields_ = [("time", C.c_double), ("n", C.c_int64), ("nvar", C.c_int),
+                ("var_stride", C.c_int64), ("id", C.c_void_p), ("lon", C.c_void_p),
+                ("lat", C.c_void_p), ("depth", C.c_void_p), ("status", C.c_void_p),
+                ("age", C.c_void_p), ("vars", C.c_void_p)]
+
+
+RECORD_CB = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(Record))
+
 _P = C.c_void_p
 _SIGS = {
     "pg_last_error": ([], C.c_char_p),
@@ -65,8 +75,15 @@ _SIGS = {
     "pg_fieldset_load_snapshot": ([_P, C.c_int, _P, C.c_int, _P], C.c_int),
     "pg_fieldset_stream": ([_P, _P, SNAPSHOT_CB, _P, C.c_int], C.c_int),
     "pg_fieldset_device_bytes": ([_P, C.POINTER(C.c_size_t)], C.c_int),
+    "pg_fieldset_set_ring": ([_P, C.c_int], C.c_int),
     "pg_fieldset_get_scale": ([_P, C.c_int, C.c_int, C.POINTER(C.c_float)], C.c_int),
     "pg_fieldset_destroy": ([_P], C.c_int),
+    "pg_fieldset_add_constant": ([_P, C.c_char_p, C.c_double], C.c_int),
+    "pg_fieldset_get_constant": ([_P, C.c_char_p, C.POINTER(C.c_double)], C.c_int),
+    "pg_fieldset_set_interp": ([_P, C.c_int], C.c_int),
+    "pg_fieldset_add_scalar": ([_P, C.c_char_p, C.c_int, C.POINTER(C.c_int)], C.c_int),
+    "pg_fieldset_load_scalar": ([_P, C.c_int, C.c_int, _P, C.c_int, _P], C.c_int),
+    "pg_pset_get_variables": ([_P, _P, _P, _P], C.c_int),
     "pg_kernel_create": ([C.c_int, C.c_uint, C.c_double, C.c_double, C.POINTER(_P)], C.c_int),
     "pg_kernel_destroy": ([_P], C.c_int),
     "pg_pset_create": ([_P, C.c_int64, _P, _P, _P, _P, C.c_double, _P, C.c_uint64, C.c_int,
@@ -77,6 +94,8 @@ _SIGS = {
     "pg_pset_set_tune": ([_P, C.POINTER(Tune)], C.c_int),
     "pg_execute": ([_P, _P, C.c_double, C.c_double, C.c_double, OUTPUT_CB, _P, _P,
                     C.POINTER(C.c_int64)], C.c_int),
+    "pg_execute_records": ([_P, _P, C.c_double, C.c_double, C.c_double, C.c_int, RECORD_CB, _P,
+                            _P, C.POINTER(C.c_int64)], C.c_int),
     "pg_pset_resort": ([_P, _P], C.c_int),
     "pg_pset_moments": ([_P, C.POINTER(C.c_double), _P], C.c_int),
     "pg_pset_save": ([_P, C.c_char_p], C.c_int),
@@ -85,6 +104,7 @@ _SIGS = {
     "pg_debug_set_alloc_limit": ([C.c_int64], C.c_int),
     "pg_pset_kernel_timing": ([_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
     "pg_launch_count": ([C.POINTER(C.c_int64)], C.c_int),
+    "pg_measure_l2_read": ([C.c_size_t, C.c_int, C.POINTER(C.c_double), _P], C.c_int),
     "pg_fieldset_stats": ([_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
     "pg_moments_f64_noalloc": ([_P, _P, _P, _P, C.c_int64, _P, _P], C.c_int),
     "pg_execute_batch": ([C.c_int, _P, _P, _P, _P, C.c_double, C.POINTER(Tune), C.POINTER(Tune),

@@ -19,6 +19,9 @@ from . import _native as N
 _MESH = {"flat": N.PG_FLAT, "spherical": N.PG_SPHERICAL}
 _STORAGE = {"f64": N.PG_F64, "f32": N.PG_F32, "f16": N.PG_F16S, "bf16": N.PG_BF16S}
 _POS = {"f64": N.PG_POS_F64, "f32": N.PG_POS_F32, "cell": N.PG_POS_CELL}
+_INTERP = {"linear": N.PG_LINEAR, "nearest": N.PG_NEAREST}
+_BEH = {"brownian": N.PG_BROWNIAN, "sink": N.PG_SINK, "settle": N.PG_SETTLE, "age": N.PG_AGE,
+        "sample": N.PG_SAMPLE}
 
 
 def _ptr(a, dtype):
@@ -99,6 +102,10 @@ class FieldSet:
         p, keep = _ptr(data, np.float64 if dt == N.PG_F64 else np.float32)
         N.check(self._lib.pg_fieldset_load_snapshot(self.h, int(s), p, dt, _stream(stream)))
 
+    def set_ring(self, slots):
+        """Slots of the streamed-snapshot ring (4..64), before :meth:`stream`."""
+        N.check(self._lib.pg_fieldset_set_ring(self.h, int(slots)))
+
     def stream(self, snapshots=None, callback: Optional[Callable] = None, dtype="f32"):
         """Stream snapshots during execute: either a list of per-snapshot arrays
         (kept alive by this object) or ``callback(s, out)`` filling a numpy view
@@ -128,6 +135,36 @@ class FieldSet:
                     return 1
             self._cb = N.SNAPSHOT_CB(cb)
             N.check(self._lib.pg_fieldset_stream(self.h, None, self._cb, None, _STORAGE[dtype]))
+
+    def add_constant(self, name, value):
+        """A named constant read by the behaviours (Sect. 3): "Kh", "w_sink",
+        "dwelling_depth", "max_age"."""
+        N.check(self._lib.pg_fieldset_add_constant(self.h, name.encode(), float(value)))
+
+    def get_constant(self, name):
+        v = C.c_double()
+        N.check(self._lib.pg_fieldset_get_constant(self.h, name.encode(), C.byref(v)))
+        return v.value
+
+    def set_interp(self, method):
+        """Spatial interpolation of the velocities: "linear" or "nearest"."""
+        N.check(self._lib.pg_fieldset_set_interp(self.h, _INTERP[method]))
+
+    def add_scalar(self, name, method="linear"):
+        """A scalar field (e.g. temperature) to sample into particle variables;
+        returns its index."""
+        i = C.c_int()
+        N.check(self._lib.pg_fieldset_add_scalar(self.h, name.encode(), _INTERP[method],
+                                                 C.byref(i)))
+        self.nscalars = i.value + 1
+        return i.value
+
+    def load_scalar(self, index, s, data, stream=None):
+        """Snapshot s of scalar field `index`, shaped (nz, ny, nx)."""
+        dt = _src_dtype(data)
+        p, keep = _ptr(data, np.float64 if dt == N.PG_F64 else np.float32)
+        N.check(self._lib.pg_fieldset_load_scalar(self.h, int(index), int(s), p, dt,
+                                                  _stream(stream)))
 
     def device_bytes(self):
         b = C.c_size_t()
@@ -164,16 +201,20 @@ class FieldSet:
 
 
 class Kernel:
-    """Advection scheme plus behaviours (Sect. 2.1.2): ``Kernel('rk4') + 'brownian'``."""
+    """Advection scheme plus behaviours (Sect. 2.1.2): ``Kernel('rk4') + 'brownian'``.
+
+    Behaviours: "brownian", "sink", "settle", "age", "sample".  kh / w_sink
+    None: the field set's constants "Kh" / "w_sink" at execute time."""
 
     def __init__(self, scheme="rk4", behaviours=(), kh=0.0, w_sink=0.0):
         self._lib = N.load()
         self.scheme = scheme
         self.behaviours = tuple(behaviours)
-        self.kh, self.w_sink = float(kh), float(w_sink)
+        self.kh = float("nan") if kh is None else float(kh)
+        self.w_sink = float("nan") if w_sink is None else float(w_sink)
         bits = 0
         for b in self.behaviours:
-            bits |= {"brownian": N.PG_BROWNIAN, "sink": N.PG_SINK}[b]
+            bits |= _BEH[b]
         h = C.c_void_p()
         N.check(self._lib.pg_kernel_create({"euler": N.PG_EULER, "rk4": N.PG_RK4}[scheme], bits,
                                            self.kh, self.w_sink, C.byref(h)))
@@ -203,6 +244,7 @@ class ParticleSet:
         self.pos = pos
         if _handle is not None:
             self.h = _handle
+            self.fieldset_nvar = getattr(fieldset, "nscalars", 0)
             return
         n = len(lon)
         pl, k1 = _ptr(lon, np.float64)
@@ -214,6 +256,7 @@ class ParticleSet:
         N.check(self._lib.pg_pset_create(fieldset.h, n, pl, pa, pd, pt, float(t0), pi,
                                          int(id_base), _POS[pos], int(seed), C.byref(h)))
         self.h = h
+        self.fieldset_nvar = getattr(fieldset, "nscalars", 0)
 
     def add(self, lon, lat, depth=None, time=None, t0=0.0, ids=None, id_base=0):
         pl, k1 = _ptr(lon, np.float64)
@@ -264,6 +307,43 @@ class ParticleSet:
                                      cb, None, _stream(stream), C.byref(steps)))
         return steps.value
 
+    def execute_records(self, kernel: Kernel, runtime, dt, output_dt, record: Callable,
+                        indexed=True, stream=None):
+        """Advance like :meth:`execute`, with the ParticleFile output of Sect. 3:
+        ``record(time, dict)`` gets, at every output time, host copies of the
+        rows (id, lon, lat, depth, status, age, vars [nvar, rows]): every
+        particle, or (indexed) those alive at that time and those deleted
+        since the previous output.  Returns particle-steps."""
+        def hook(user, rp):
+            try:
+                r = rp.contents
+                n = r.n
+
+                def arr(p, ct, dt, m=n):
+                    return np.ctypeslib.as_array((ct * m).from_address(p)).view(dt).copy() \
+                        if m else np.zeros(0, dt)
+                out = dict(id=arr(r.id, C.c_uint64, np.uint64), lon=arr(r.lon, C.c_double, np.float64),
+                           lat=arr(r.lat, C.c_double, np.float64),
+                           depth=arr(r.depth, C.c_double, np.float64),
+                           status=arr(r.status, C.c_uint8, np.uint8),
+                           age=arr(r.age, C.c_double, np.float64))
+                vs = np.zeros((r.nvar, n))
+                for j in range(r.nvar):
+                    if n:
+                        vs[j] = np.ctypeslib.as_array(
+                            (C.c_double * n).from_address(r.vars + 8 * j * r.var_stride))
+                out["vars"] = vs
+                res = record(r.time, out)
+                return 0 if res is None else int(res)
+            except Exception:
+                return 1
+        cb = N.RECORD_CB(hook)
+        steps = C.c_int64()
+        N.check(self._lib.pg_execute_records(self.h, kernel.h, float(runtime), float(dt),
+                                             float(output_dt), int(bool(indexed)), cb, None,
+                                             _stream(stream), C.byref(steps)))
+        return steps.value
+
     def get(self, sort_by_id=True, stream=None):
         """Host copy of the state: dict of lon, lat, depth, time, id, step, status."""
         n = len(self)
@@ -279,6 +359,25 @@ class ParticleSet:
             o = np.argsort(out["id"], kind="stable")
             out = {k: v[o] for k, v in out.items()}
         return out
+
+    def get_variables(self, sort_by_id=True, stream=None):
+        """Host copy of the particle variables: dict of age [n] and vars
+        [nvar, n] (sampled scalar fields), in id order by default."""
+        n = len(self)
+        nvar = self.fieldset_nvar
+        age = np.empty(n)
+        var = np.empty((nvar, n))
+        if n:
+            N.check(self._lib.pg_pset_get_variables(self.h, age.ctypes.data,
+                                                    var.ctypes.data if nvar else None,
+                                                    _stream(stream)))
+            if sort_by_id:
+                ids = np.empty(n, np.uint64)
+                N.check(self._lib.pg_pset_get(self.h, None, None, None, None, ids.ctypes.data,
+                                              None, None, _stream(stream)))
+                o = np.argsort(ids, kind="stable")
+                age, var = age[o], var[:, o]
+        return dict(age=age, vars=var)
 
     def get_into(self, lon=None, lat=None, depth=None, time=None, ids=None, status=None,
                  stream=None):

@@ -34,6 +34,9 @@ UNITS = {
     "surrogate.cu": [],
     "advect_f32.cu": ([f"-maxrregcount={os.environ['PG_MAXRREG']}"]
                       if os.environ.get("PG_MAXRREG") else []),
+    "advect_f32_ext.cu": [],
+    "probe.cu": [],
+    "output.cu": [],
 }
 
 

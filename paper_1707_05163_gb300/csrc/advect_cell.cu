@@ -75,9 +75,10 @@ __global__ void from_cell_kernel(GridArgs g, const int32_t *ci, const int32_t *c
                                  int64_t n) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
-    if (lon) lon[p] = g.x0[0] + ((double)ci[p] + (double)fx[p]) * g.d[0];
-    if (lat) lat[p] = g.x0[1] + ((double)cj[p] + (double)fy[p]) * g.d[1];
-    if (dep) dep[p] = g.nz > 1 ? g.x0[2] + ((double)ck[p] + (double)fz[p]) * g.d[2] : 0.0;
+    // x0 + (i + f) d with one rounding of the product-sum (fused multiply-add)
+    if (lon) lon[p] = __fma_rn((double)ci[p] + (double)fx[p], g.d[0], g.x0[0]);
+    if (lat) lat[p] = __fma_rn((double)cj[p] + (double)fy[p], g.d[1], g.x0[1]);
+    if (dep) dep[p] = g.nz > 1 ? __fma_rn((double)ck[p] + (double)fz[p], g.d[2], g.x0[2]) : 0.0;
   }
 }
 

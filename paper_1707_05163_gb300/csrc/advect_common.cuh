@@ -430,6 +430,23 @@ __device__ __forceinline__ float weighted_sum(const float (&v)[NC], const float 
   return acc;
 }
 
+// Nearest-neighbour pick among the corners of the cached cell: corner index
+// (i + 1 if xi > 1/2) + 2 (j + 1 if eta > 1/2) + 4 (k + 1 if zeta > 1/2), the
+// lower node on a tie.  A select chain, so a NaN at another corner does not
+// reach the result.
+template <int NC, typename Real>
+__device__ __forceinline__ Real pick_corner(const Real (&v)[NC], int qi) {
+  Real r = v[0];
+#pragma unroll
+  for (int q = 1; q < NC; ++q) r = (qi == q) ? v[q] : r;
+  return r;
+}
+
+template <typename Real>
+__device__ __forceinline__ int nearest_corner(Real xi, Real eta, Real zeta) {
+  return (xi > (Real)0.5 ? 1 : 0) | (eta > (Real)0.5 ? 2 : 0) | (zeta > (Real)0.5 ? 4 : 0);
+}
+
 // FP32 field values from the cached corners: spatial interpolation in both
 // snapshots (weighted_sum), then (1 - tau) a + tau b, exact at both ends, so a stage time on
 // a snapshot gives the same value from either neighbouring interval (results
@@ -454,6 +471,22 @@ __device__ __forceinline__ int interp32(const Sampler<float, Store, NF, D3, GEO>
   if constexpr (NF == 2) vel[2] = 0.f;
   if (CHECK && (!(vel[0] == vel[0]) | !(vel[1] == vel[1]) | !(vel[2] == vel[2]))) return 3;
   return 0;
+}
+
+// FP32 nearest-neighbour values: the nearest corner in each snapshot, then
+// (1 - tau) a + tau b.
+template <typename Store, int NF, bool D3, int GEO>
+__device__ __forceinline__ void nearest32(const Sampler<float, Store, NF, D3, GEO> &c, float xi,
+                                          float eta, float zeta, float tau, float (&vel)[3]) {
+  constexpr int NC = Sampler<float, Store, NF, D3, GEO>::NC;
+  const int qi = nearest_corner(xi, eta, D3 ? zeta : 0.f);
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const float va = pick_corner<NC>(c.v[0][f], qi);
+    const float vb = pick_corner<NC>(c.v[1][f], qi);
+    vel[f] = fmaf(tau, vb, (1.0f - tau) * va);
+  }
+  if constexpr (NF == 2) vel[2] = 0.f;
 }
 
 // Field values (m/s) at a stage, once the cell (c.ci, c.cj, c.ck) and the
@@ -491,11 +524,14 @@ __device__ __forceinline__ int sample_fields(const A &a, Sampler<Real, Store, NF
       if (!gather(a, c, steady)) return -1;
     }
     constexpr int NC = Sampler<Real, Store, NF, D3, GEO>::NC;
+    const int qi = nearest_corner(xi, eta, D3 ? zeta : (Real)0);
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      Real val = interp_space<Real, NC>(c.v[0][f], xi, eta, zeta);
+      Real val = a.f.nearest ? pick_corner<NC>(c.v[0][f], qi)
+                             : interp_space<Real, NC>(c.v[0][f], xi, eta, zeta);
       if (!steady) {
-        const Real b = interp_space<Real, NC>(c.v[1][f], xi, eta, zeta);
+        const Real b = a.f.nearest ? pick_corner<NC>(c.v[1][f], qi)
+                                   : interp_space<Real, NC>(c.v[1][f], xi, eta, zeta);
         val = val + (b - val) * tau;
       }
       if (!(val == val)) return 3;
@@ -504,6 +540,92 @@ __device__ __forceinline__ int sample_fields(const A &a, Sampler<Real, Store, NF
     if constexpr (NF == 2) vel[2] = (Real)0;
     return 0;
   }
+}
+
+// ------------------------------------------------------ scalar fields ---
+// Value of scalar field q (a tracer such as temperature, Sect. 3) at a
+// position and time, in FP64 with every product and sum rounded separately
+// (no fused multiply-add, in the order of the definition): the cell on each
+// axis by a full search, the wrap cell on a periodic zonal axis, bilinear
+// weights applied as (w00 f00 + w10 f10) + (w11 f11 + w01 f01), linear in
+// depth between two levels, or the nearest node; linear in time.  Positions
+// are inside the domain when this is called.  Returns false (and records an
+// internal error) when a snapshot is missing or the time is outside a
+// non-periodic field.
+template <typename TS>
+__device__ __forceinline__ double tracer_node(const TS *b, const GridArgs &g, int k, int j, int i) {
+  return (double)b[((size_t)k * g.ny + (size_t)j) * g.nx + (size_t)i];
+}
+
+__device__ __forceinline__ double lerp_rn(double a, double b, double w) {
+  return __dadd_rn(a, __dmul_rn(__dadd_rn(b, -a), w));      // a + (b - a) w
+}
+
+template <typename TS>
+__device__ __noinline__ bool tracer_value(const GridArgs &g, const FieldArgs &f, int q, double lon,
+                                          double lat, double dep, double t, double &out, int *err) {
+  int i0, i1;
+  double xi;
+  if (g.periodic) {
+    const double p = wrap_lon(lon, g.lon[0]);
+    if (p >= g.lon[g.nx - 1]) {
+      i0 = g.nx - 1; i1 = 0;
+      xi = __ddiv_rn(__dadd_rn(p, -g.lon[g.nx - 1]), __dadd_rn(g.lon_end, -g.lon[g.nx - 1]));
+    } else {
+      i0 = axis_search<double>(g, 0, g.nx, p); i1 = i0 + 1;
+      xi = __ddiv_rn(__dadd_rn(p, -g.lon[i0]), __dadd_rn(g.lon[i1], -g.lon[i0]));
+    }
+  } else {
+    i0 = axis_search<double>(g, 0, g.nx, lon); i1 = i0 + 1;
+    xi = __ddiv_rn(__dadd_rn(lon, -g.lon[i0]), __dadd_rn(g.lon[i1], -g.lon[i0]));
+  }
+  const int j0 = axis_search<double>(g, 1, g.ny, lat), j1 = j0 + 1;
+  const double eta = __ddiv_rn(__dadd_rn(lat, -g.lat[j0]), __dadd_rn(g.lat[j1], -g.lat[j0]));
+  int k0 = 0, k1 = 0;
+  double zeta = 0.0;
+  if (g.nz > 1) {
+    k0 = axis_search<double>(g, 2, g.nz, dep); k1 = k0 + 1;
+    zeta = __ddiv_rn(__dadd_rn(dep, -g.depth[k0]), __dadd_rn(g.depth[k1], -g.depth[k0]));
+  }
+  int s0 = 0, s1 = 0;
+  double tau = 0.0;
+  if (f.nt > 1) {
+    double tt, ta, tb;
+    s0 = -1;
+    if (!time_interval(f, t, s0, s1, tt, ta, tb)) {
+      atomicCAS(err, 0, (int)DEVERR_TIME_RANGE);
+      return false;
+    }
+    tau = __ddiv_rn(__dadd_rn(tt, -ta), __dadd_rn(tb, -ta));
+  }
+  double val[2] = {0.0, 0.0};
+  for (int r = 0; r < (f.nt > 1 ? 2 : 1); ++r) {
+    const TS *b = reinterpret_cast<const TS *>(f.ttab[q * f.nt + (r == 0 ? s0 : s1)]);
+    if (b == nullptr) {
+      atomicCAS(err, 0, (int)DEVERR_SLAB_MISSING);
+      return false;
+    }
+    if (f.tnearest[q]) {
+      val[r] = tracer_node(b, g, zeta > 0.5 ? k1 : k0, eta > 0.5 ? j1 : j0, xi > 0.5 ? i1 : i0);
+    } else {
+      const double w00 = __dmul_rn(__dadd_rn(1.0, -xi), __dadd_rn(1.0, -eta));
+      const double w10 = __dmul_rn(xi, __dadd_rn(1.0, -eta));
+      const double w11 = __dmul_rn(xi, eta);
+      const double w01 = __dmul_rn(__dadd_rn(1.0, -xi), eta);
+      double lev[2] = {0.0, 0.0};
+      for (int kk = 0; kk < (g.nz > 1 ? 2 : 1); ++kk) {
+        const int k = kk ? k1 : k0;
+        lev[kk] = __dadd_rn(__dadd_rn(__dmul_rn(w00, tracer_node(b, g, k, j0, i0)),
+                                      __dmul_rn(w10, tracer_node(b, g, k, j0, i1))),
+                            __dadd_rn(__dmul_rn(w11, tracer_node(b, g, k, j1, i1)),
+                                      __dmul_rn(w01, tracer_node(b, g, k, j1, i0))));
+      }
+      val[r] = g.nz > 1 ? __dadd_rn(__dmul_rn(__dadd_rn(1.0, -zeta), lev[0]), __dmul_rn(zeta, lev[1]))
+                        : lev[0];
+    }
+  }
+  out = f.nt > 1 ? lerp_rn(val[0], val[1], tau) : val[0];
+  return true;
 }
 
 }  // namespace pg

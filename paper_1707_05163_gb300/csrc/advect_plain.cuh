@@ -20,6 +20,8 @@
 //     and no FP64 arithmetic runs per stage.
 #pragma once
 
+#include <type_traits>
+
 #include "advect_common.cuh"
 
 namespace pg {
@@ -106,7 +108,7 @@ __device__ __forceinline__ void relocate32(const GridArgs &g, int a, int n, floa
 // Velocity in position units per second at a stage (stage time = step start
 // + off).  Returns 0 or a particle status (PG_OOB_*, PG_NAN); -1 for an
 // internal failure already recorded in a.err.
-template <typename Real, typename Store, int NF, bool D3, int GEO, class A>
+template <bool EXT, typename Real, typename Store, int NF, bool D3, int GEO, class A>
 __device__ __forceinline__ int velocity(const A &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                         Clock &ck, Real off, Real lon, Real lat, Real dep,
                                         Real (&vel)[3]) {
@@ -168,8 +170,13 @@ __device__ __forceinline__ int velocity(const A &a, Sampler<Real, Store, NF, D3,
     xi = (q - c.xlo) * c.rx;
     eta = (lat - c.ylo) * c.ry;
     if constexpr (D3) zeta = (dep - c.zlo) * c.rz;
-    const int r = interp32<Store, NF, D3, GEO, false>(c, xi, eta, zeta, tau32(a, c, ck, off), vel);
-    if (r) return r;
+    if constexpr (EXT) {
+      if (a.f.nearest) nearest32(c, xi, eta, zeta, tau32(a, c, ck, off), vel);
+      else interp32<Store, NF, D3, GEO, false>(c, xi, eta, zeta, tau32(a, c, ck, off), vel);
+    } else {
+      const int r = interp32<Store, NF, D3, GEO, false>(c, xi, eta, zeta, tau32(a, c, ck, off), vel);
+      if (r) return r;
+    }
     if (is_sph<GEO>(g)) {
       vel[0] = lon_rate(vel[0], lat, a.k);
       vel[1] = lat_rate(vel[1], a.k);
@@ -193,13 +200,23 @@ __device__ __forceinline__ int velocity(const A &a, Sampler<Real, Store, NF, D3,
   return 0;
 }
 
+// Parameters of the worked example's behaviours per Real.
+__device__ __forceinline__ double dwell_of(const KernArgs &k, double) { return k.dwell; }
+__device__ __forceinline__ float dwell_of(const KernArgs &k, float) { return k.dwell_f; }
+
 // One step of Eq. 1.  Returns 0 and updates (lon, lat, dep) on success.
 // RK4 stages run in a loop: stage s samples at (X + k_{s-1} c_s h, t + c_s h)
 // with c = (0, 1/2, 1/2, 1) and accumulates ((k1 + 2 k2) + 2 k3) + k4.
-template <typename Real, typename Store, int NF, bool D3, int GEO, class A>
+// With the worked example's behaviours (EXT, and always in FP64): settle
+// after sinking; after the step is applied, age += |h| (the step's exact FP64
+// length h64) and STATUS_DELETED is returned, state updated, once the age
+// reaches the maximum.
+template <bool EXT, typename Real, typename Store, int NF, bool D3, int GEO, class A>
 __device__ __forceinline__ int step_one(const A &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                         Clock &ck, Real &lon, Real &lat, Real &dep, Real hr,
-                                        const uint64_t *idp, uint32_t stp) {
+                                        double h64, double &age, const uint64_t *idp,
+                                        uint32_t stp) {
+  constexpr bool X = EXT || sizeof(Real) == 8;
   Real kc[3] = {(Real)0, (Real)0, (Real)0};
   Real acc[3];
   const Real half = (Real)0.5 * hr;
@@ -214,7 +231,7 @@ __device__ __forceinline__ int step_one(const A &a, Sampler<Real, Store, NF, D3,
       const float off = (s == 0 ? 0.f : (s == 3 ? 1.f : 0.5f)) * hr;
       const float px = fmaf(kc[0], off, lon), py = fmaf(kc[1], off, lat);
       const float pz = fmaf(kc[2], off, dep);
-      if ((r = velocity(a, c, ck, off, px, py, pz, kc))) return r;
+      if ((r = velocity<EXT>(a, c, ck, off, px, py, pz, kc))) return r;
       const float wg = (s == 1 || s == 2) ? 2.f : 1.f;
       acc[0] = fmaf(wg, kc[0], acc[0]);
       acc[1] = fmaf(wg, kc[1], acc[1]);
@@ -230,7 +247,7 @@ __device__ __forceinline__ int step_one(const A &a, Sampler<Real, Store, NF, D3,
       py = lat + kc[1] * off;
       pz = dep + kc[2] * off;
     }
-    if ((r = velocity(a, c, ck, off, px, py, pz, kc))) return r;
+    if ((r = velocity<EXT>(a, c, ck, off, px, py, pz, kc))) return r;
     if (s == 0) {
       acc[0] = kc[0]; acc[1] = kc[1]; acc[2] = kc[2];
     } else if (s == 3) {
@@ -270,6 +287,20 @@ __device__ __forceinline__ int step_one(const A &a, Sampler<Real, Store, NF, D3,
     nlat = nlat + dy;
   }
   if (a.k.beh & 2u) ndep = ndep + w_of(a.k, hr) * hr;
+  bool dwelling = false;   // settle: the step starts at the dwelling depth
+  if constexpr (X) {
+    if (a.k.beh & BEH_SETTLE) {
+      const Real zd = dwell_of(a.k, hr);
+      if (dep == zd) {
+        dwelling = true;
+        ndep = zd;
+      } else {
+        Real moved = ndep + w_of(a.k, hr) * hr;
+        if ((dep - zd) * (moved - zd) <= (Real)0) moved = zd;
+        ndep = moved;
+      }
+    }
+  }
   if (is_per<GEO>(a.g)) nlon = wrap_lon(nlon, axis_lo(a.g, 0, nlon));
   if ((r = out_of_domain<Real, GEO>(a.g, nlon, nlat, ndep, D3))) {
     // FP32: a NaN result comes from a NaN stage velocity (see velocity)
@@ -279,20 +310,45 @@ __device__ __forceinline__ int step_one(const A &a, Sampler<Real, Store, NF, D3,
     return r;
   }
   lon = nlon; lat = nlat; dep = ndep;
+  if constexpr (X) {
+    if (a.k.beh & BEH_AGE) {
+      if (!(a.k.beh & BEH_SETTLE) || dwelling) age = age + fabs(h64);
+      if (age >= a.k.max_age) return STATUS_DELETED;
+    }
+  }
   return 0;
+}
+
+// Scalar fields sampled at a particle's state into its variables (the
+// sample behaviour).  Sampling after every step and sampling once at the end
+// of a chunk give the same variables: each sample overwrites the last, and
+// the state at the end of the chunk is the state after its last step.
+template <typename Store, class A>
+__device__ __forceinline__ void sample_variables(const A &a, int64_t p, double lon, double lat,
+                                                 double dep, double t) {
+  using TS = typename std::conditional<std::is_same<Store, double>::value, double, float>::type;
+  for (int q = 0; q < a.f.ntr; ++q) {
+    double v;
+    if (tracer_value<TS>(a.g, a.f, q, lon, lat, dep, t, v, a.err)) a.p.var[q * a.p.vstride + p] = v;
+  }
 }
 
 // The chunk kernel: each thread advances one particle while its time is
 // before t_stop and t_end (in the direction of dt), shortening only the step
 // that lands on t_end.  Returns the number of steps taken.
-template <typename Real, typename Store, int NF, bool D3, int GEO, class A>
+template <bool EXT, typename Real, typename Store, int NF, bool D3, int GEO, class A>
 __device__ __forceinline__ unsigned long long advance_particle(const A &a, int64_t p) {
+  constexpr bool X = EXT || sizeof(Real) == 8;
   unsigned long long done = 0;
   {
-    Real *X = reinterpret_cast<Real *>(a.p.x);
-    Real *Y = reinterpret_cast<Real *>(a.p.y);
-    Real *Z = reinterpret_cast<Real *>(a.p.z);
-    Real lon = X[p], lat = Y[p], dep = Z[p];
+    double age = 0.0;
+    if constexpr (X) {
+      if (a.k.beh & BEH_AGE) age = a.p.age[p];
+    }
+    Real *PX = reinterpret_cast<Real *>(a.p.x);
+    Real *PY = reinterpret_cast<Real *>(a.p.y);
+    Real *PZ = reinterpret_cast<Real *>(a.p.z);
+    Real lon = PX[p], lat = PY[p], dep = PZ[p];
     double t = a.p.time[p];
     uint32_t stp = a.p.step[p];
     const uint64_t *idp = a.p.id + p;   // read by the Brownian step only
@@ -308,7 +364,14 @@ __device__ __forceinline__ unsigned long long advance_particle(const A &a, int64
         double h = a.dt;
         if (sgn * (a.t_end - t) < sgn * h) h = a.t_end - t;
         ck.t = t;
-        const int r = step_one(a, c, ck, lon, lat, dep, (Real)h, idp, stp);
+        const int r = step_one<EXT>(a, c, ck, lon, lat, dep, (Real)h, h, age, idp, stp);
+        if (r == STATUS_DELETED) {      // taken, then deleted by the age behaviour
+          t = t + h;
+          ++stp;
+          ++done;
+          st = (uint8_t)r;
+          break;
+        }
         if (r > 0) { st = (uint8_t)r; break; }
         if (r < 0) break;
         t = t + h;
@@ -331,8 +394,17 @@ __device__ __forceinline__ unsigned long long advance_particle(const A &a, int64
       for (; k < n; ++k) {
         ck.k = k;
         const float h = (k == n - 1) ? hlf : hf;
-        const int r = step_one(a, c, ck, lon, lat, dep, (Real)h, idp, stp);
-        if (r > 0) { st = (uint8_t)r; break; }
+        const int r = step_one<EXT>(a, c, ck, lon, lat, dep, (Real)h,
+                                    (k == n - 1) ? hlast : a.dt, age, idp, stp);
+        if (r > 0) {
+          if (X && r == STATUS_DELETED) {   // taken, then deleted by the age behaviour
+            ++stp;
+            ck.d += h;
+            ++k;
+          }
+          st = (uint8_t)r;
+          break;
+        }
         if (r < 0) break;
         ++stp;
         ck.d += h;
@@ -341,10 +413,15 @@ __device__ __forceinline__ unsigned long long advance_particle(const A &a, int64
       if (k == n && n > 0) t = (hlast != a.dt) ? a.t_end : t + (double)n * a.dt;
       else t = t + (double)k * a.dt;
     }
-    X[p] = lon; Y[p] = lat; Z[p] = dep;
+    PX[p] = lon; PY[p] = lat; PZ[p] = dep;
     a.p.time[p] = t;
     a.p.step[p] = stp;
     a.p.status[p] = st;
+    if constexpr (X) {
+      if (a.k.beh & BEH_AGE) a.p.age[p] = age;
+      if ((a.k.beh & BEH_SAMPLE) && done > 0)
+        sample_variables<Store>(a, p, (double)lon, (double)lat, (double)dep, t);
+    }
   }
   return done;
 }
@@ -360,11 +437,15 @@ __device__ __forceinline__ void count_steps(unsigned long long done, unsigned lo
 // faster than the unbounded allocation despite a few spilled words, as more
 // resident warps hide the gather and dependency latencies.  FP32 2-D: at most
 // 85 registers, six 128-thread blocks (24 warps) per SM.
-template <typename Real, typename Store, int NF, bool D3, int GEO>
+//
+// EXT = true: the FP32 kernel with the worked example's behaviours (settle,
+// age, sampled variables) and nearest-neighbour interpolation; the FP64
+// kernel always has them.
+template <typename Real, typename Store, int NF, bool D3, int GEO, bool EXT = false>
 __global__ void __launch_bounds__(sizeof(Real) == 4 && !D3 ? 128 : 256, sizeof(Real) == 4 ? (D3 ? 2 : 6) : 1) advect_plain_kernel(StepArgs a) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long done = 0;
-  if (p < a.p.n && a.p.status[p] == 0) done = advance_particle<Real, Store, NF, D3, GEO>(a, p);
+  if (p < a.p.n && a.p.status[p] == 0) done = advance_particle<EXT, Real, Store, NF, D3, GEO>(a, p);
   count_steps(done, a.steps_done);
 }
 
@@ -427,7 +508,7 @@ __global__ void __launch_bounds__(256, 2) advect_batch_kernel(const __grid_const
     if (t >= b.ntiles) break;
     const BatchStep v{b.g, b.f, sk, sp, sdt, b.t_stop, st_end, b.steps_done, b.err};
     const int64_t p = (int64_t)b.tiles[t].y + threadIdx.x;
-    if (p < sp.n && sp.status[p] == 0) done += advance_particle<float, Store, NF, D3, GEO>(v, p);
+    if (p < sp.n && sp.status[p] == 0) done += advance_particle<false, float, Store, NF, D3, GEO>(v, p);
     __syncthreads();
   }
   count_steps(done, b.steps_done);

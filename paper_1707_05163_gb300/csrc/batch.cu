@@ -240,6 +240,15 @@ extern "C" pg_status pg_execute_batch(int nrel, pg_pset *const *psets,
     t_end_max = std::max(t_end_max, p->t_min + runtime[r]);
   }
   pg_fieldset *fs = B.fs;
+  if (fs->interp != PG_LINEAR) {
+    set_error("batched execution interpolates linearly");
+    return PG_ERR_UNSUPPORTED;
+  }
+  for (int r = 0; r < nrel; ++r)
+    if (kernels[r]->beh & (PG_SETTLE | PG_AGE | PG_SAMPLE)) {
+      set_error("batched execution runs advection, Brownian motion and sinking only (release %d)", r);
+      return PG_ERR_UNSUPPORTED;
+    }
   if (fs->streaming || fs->nt < 1) {
     set_error("batched execution needs all snapshots resident");
     return PG_ERR_UNSUPPORTED;
@@ -262,7 +271,6 @@ extern "C" pg_status pg_execute_batch(int nrel, pg_pset *const *psets,
   // release table and work list (tiles of 32 particles x blocks later: tile
   // length is the block size, so tiles are rebuilt per block size)
   B.rel.resize(nrel);
-  const double D = 1852.0 * 60.0;
   std::vector<double> weight(nrel);
   for (int r = 0; r < nrel; ++r) {
     pg_pset *p = psets[r];
@@ -272,10 +280,10 @@ extern "C" pg_status pg_execute_batch(int nrel, pg_pset *const *psets,
     R.p.n = p->n;
     R.p.x = p->x; R.p.y = p->y; R.p.z = p->z;
     R.p.time = p->time; R.p.id = p->id; R.p.step = p->step; R.p.status = p->status;
-    R.k.scheme = k->scheme; R.k.beh = k->beh; R.k.kh = k->kh; R.k.w_sink = k->w_sink;
-    R.k.seed = p->seed; R.k.deg_m = D;
-    R.k.deg_m_f = (float)D; R.k.inv_deg_m_f = (float)(1.0 / D);
-    R.k.kh_f = (float)k->kh; R.k.w_sink_f = (float)k->w_sink;
+    {
+      const pg_status rk = resolve_kernel(k, fs, p->seed, R.k);
+      if (rk) return rk;
+    }
     R.dt = dt[r];
     R.t_end = p->t_min + runtime[r];
     weight[r] = (double)(k->scheme == PG_RK4 ? 4 : 1) * std::min(window, runtime[r]) / dt[r] *

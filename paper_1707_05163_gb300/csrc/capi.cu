@@ -50,6 +50,7 @@ void dev_free(void *p) {
 }
 
 cudaError_t launch_resort(pg_pset *ps, cudaStream_t st, int64_t *n_alive);
+cudaError_t prepare_resort(pg_pset *ps);
 cudaError_t launch_moments(const pg_pset *ps, double *out7, cudaStream_t st);
 
 }  // namespace pg
@@ -153,10 +154,23 @@ pg_status upload_coord(const double *src, int64_t n, void *dst, int pos, double 
     return PG_OK;
   }
   if (!is_device_ptr(src)) {
-    std::vector<float> h((size_t)n);
-    for (int64_t i = 0; i < n; ++i) h[i] = (float)src[i];
-    CU(cudaMemcpyAsync(dst, h.data(), n * 4, cudaMemcpyHostToDevice, st));
-    CU(cudaStreamSynchronize(st));
+    // host source: copy the FP64 values to the device (at the copy engines'
+    // rate from pinned memory) and round them there
+    double *tmp = nullptr;
+    CU(dev_alloc((void **)&tmp, (size_t)n * 8));
+    cudaError_t e = cudaMemcpyAsync(tmp, src, n * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+      f64_to_f32_kernel<<<grid_for(n, sm), 256, 0, st>>>(tmp, (float *)dst, n);
+      note_launches(1);
+      e = cudaGetLastError();
+    }
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    dev_free(tmp);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+      set_error("particle upload failed: %s", cudaGetErrorString(e));
+      return PG_ERR_CUDA;
+    }
     return PG_OK;
   }
   f64_to_f32_kernel<<<grid_for(n, sm), 256, 0, st>>>(src, (float *)dst, n);
@@ -168,7 +182,7 @@ pg_status upload_coord(const double *src, int64_t n, void *dst, int pos, double 
 }  // namespace
 
 namespace pg {
-pg_status alloc_arrays(PsetArrays &A, int pos, int64_t cap) {
+pg_status alloc_arrays(PsetArrays &A, int pos, int64_t cap, int nvar) {
   const size_t n = (size_t)std::max<int64_t>(cap, 1);
   cudaError_t e = cudaSuccess;
   auto al = [&](void **p, size_t b) {
@@ -185,6 +199,8 @@ pg_status alloc_arrays(PsetArrays &A, int pos, int64_t cap) {
   al((void **)&A.id, n * 8);
   al((void **)&A.step, n * 4);
   al((void **)&A.status, n);
+  al((void **)&A.age, n * 8);
+  if (nvar > 0) al((void **)&A.var, n * 8 * (size_t)nvar);
   if (e != cudaSuccess) {
     A.free_all();
     cudaGetLastError();
@@ -199,29 +215,24 @@ pg_status alloc_arrays(PsetArrays &A, int pos, int64_t cap) {
 
 namespace {
 
-PsetArrays arrays_of(const pg_pset *ps) {
-  PsetArrays A;
-  A.x = ps->x; A.y = ps->y; A.z = ps->z;
-  A.ci = ps->ci; A.cj = ps->cj; A.ck = ps->ck;
-  A.fx = ps->fx; A.fy = ps->fy; A.fz = ps->fz;
-  A.time = ps->time; A.id = ps->id; A.step = ps->step; A.status = ps->status;
-  return A;
-}
+PsetArrays arrays_of(const pg_pset *ps) { return pset_arrays(ps); }
+void set_arrays(pg_pset *ps, const PsetArrays &A) { pset_set_arrays(ps, A); }
 
-void set_arrays(pg_pset *ps, const PsetArrays &A) {
-  ps->x = A.x; ps->y = A.y; ps->z = A.z;
-  ps->ci = A.ci; ps->cj = A.cj; ps->ck = A.ck;
-  ps->fx = A.fx; ps->fy = A.fy; ps->fz = A.fz;
-  ps->time = A.time; ps->id = A.id; ps->step = A.step; ps->status = A.status;
-}
-
-// The device arrays holding a particle set's state, with element sizes.
-std::vector<std::pair<void *, size_t>> state_arrays(const PsetArrays &A, int pos) {
-  if (pos == PG_POS_CELL)
-    return {{A.ci, 4}, {A.cj, 4}, {A.ck, 4}, {A.fx, 4}, {A.fy, 4}, {A.fz, 4},
-            {A.time, 8}, {A.id, 8}, {A.step, 4}, {A.status, 1}};
-  const size_t el = pos_elem(pos);
-  return {{A.x, el}, {A.y, el}, {A.z, el}, {A.time, 8}, {A.id, 8}, {A.step, 4}, {A.status, 1}};
+// The device arrays holding a particle set's state (n entries each from the
+// given pointer), with element sizes; variable j starts at var + j * cap.
+std::vector<std::pair<void *, size_t>> state_arrays(const PsetArrays &A, int pos, int nvar,
+                                                    int64_t cap) {
+  std::vector<std::pair<void *, size_t>> v;
+  if (pos == PG_POS_CELL) {
+    v = {{A.ci, 4}, {A.cj, 4}, {A.ck, 4}, {A.fx, 4}, {A.fy, 4}, {A.fz, 4},
+         {A.time, 8}, {A.id, 8}, {A.step, 4}, {A.status, 1}};
+  } else {
+    const size_t el = pos_elem(pos);
+    v = {{A.x, el}, {A.y, el}, {A.z, el}, {A.time, 8}, {A.id, 8}, {A.step, 4}, {A.status, 1}};
+  }
+  v.push_back({A.age, 8});
+  for (int j = 0; j < nvar; ++j) v.push_back({A.var ? A.var + (size_t)j * cap : nullptr, 8});
+  return v;
 }
 
 GridArgs grid_args(const pg_fieldset *fs) {
@@ -259,6 +270,24 @@ GridArgs grid_args(const pg_fieldset *fs) {
 }  // namespace
 
 GridArgs pg::grid_args_of(const pg_fieldset *fs) { return grid_args(fs); }
+
+PsetArrays pg::pset_arrays(const pg_pset *ps) {
+  PsetArrays A;
+  A.x = ps->x; A.y = ps->y; A.z = ps->z;
+  A.ci = ps->ci; A.cj = ps->cj; A.ck = ps->ck;
+  A.fx = ps->fx; A.fy = ps->fy; A.fz = ps->fz;
+  A.time = ps->time; A.id = ps->id; A.step = ps->step; A.status = ps->status;
+  A.age = ps->age; A.var = ps->var;
+  return A;
+}
+
+void pg::pset_set_arrays(pg_pset *ps, const PsetArrays &A) {
+  ps->x = A.x; ps->y = A.y; ps->z = A.z;
+  ps->ci = A.ci; ps->cj = A.cj; ps->ck = A.ck;
+  ps->fx = A.fx; ps->fy = A.fy; ps->fz = A.fz;
+  ps->time = A.time; ps->id = A.id; ps->step = A.step; ps->status = A.status;
+  ps->age = A.age; ps->var = A.var;
+}
 
 namespace {
 
@@ -340,7 +369,7 @@ pg_status upload_to_slot(pg_fieldset *fs, Slot &sl, int s) {
 pg_status ensure_slots(pg_fieldset *fs, const std::vector<int> &need, int prefetch,
                        cudaStream_t st) {
   auto find = [&](int s) {
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < (int)fs->slot.size(); ++q)
       if (fs->slot[q].s == s) return q;
     return -1;
   };
@@ -350,12 +379,12 @@ pg_status ensure_slots(pg_fieldset *fs, const std::vector<int> &need, int prefet
   for (int s : need) {
     if (find(s) >= 0) continue;
     int q = -1;
-    for (int c = 0; c < 4 && q < 0; ++c)
+    for (int c = 0; c < (int)fs->slot.size() && q < 0; ++c)
       if (!needed(c) && fs->slot[c].s != prefetch) q = c;
-    for (int c = 0; c < 4 && q < 0; ++c)
+    for (int c = 0; c < (int)fs->slot.size() && q < 0; ++c)
       if (!needed(c)) q = c;
     if (q < 0) {
-      set_error("streamed field needs more than four resident snapshots per chunk");
+      set_error("streamed field needs more resident snapshots per chunk than its ring holds");
       return PG_ERR_UNSUPPORTED;
     }
     pg_status r = upload_to_slot(fs, fs->slot[q], s);
@@ -373,7 +402,7 @@ pg_status ensure_slots(pg_fieldset *fs, const std::vector<int> &need, int prefet
   CU(cudaMemcpyAsync(fs->d_tab, tab.data(), sizeof(void *) * fs->nt, cudaMemcpyHostToDevice, st));
   if (prefetch >= 0 && find(prefetch) < 0) {
     int q = -1;
-    for (int c = 0; c < 4 && q < 0; ++c)
+    for (int c = 0; c < (int)fs->slot.size() && q < 0; ++c)
       if (!needed(c)) q = c;
     if (q >= 0) {
       pg_status r = upload_to_slot(fs, fs->slot[q], prefetch);
@@ -384,7 +413,7 @@ pg_status ensure_slots(pg_fieldset *fs, const std::vector<int> &need, int prefet
 }
 
 void mark_slots_used(pg_fieldset *fs, const std::vector<int> &need, cudaStream_t st) {
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < (int)fs->slot.size(); ++q)
     if (std::find(need.begin(), need.end(), fs->slot[q].s) != need.end())
       cudaEventRecord(fs->slot[q].free, st);
 }
@@ -413,7 +442,67 @@ void free_resident(pg_fieldset *fs) {
   fs->slabs.clear();
 }
 
+void free_tracers(pg_fieldset *fs) {
+  for (void *p : fs->tr_slabs) dev_free(p);
+  fs->tr_slabs.assign(fs->tr_slabs.size(), nullptr);
+}
+
+// Initial variables of particles [off, off + n): age 0, sampled values NaN
+// (nothing sampled yet).
+pg_status init_variables(pg_pset *ps, int64_t off, int64_t n, cudaStream_t st) {
+  if (n <= 0) return PG_OK;
+  const int sm = ps->fs->sm_count;
+  fill_f64_kernel<<<grid_for(n, sm), 256, 0, st>>>(ps->age + off, 0.0, n);
+  note_launches(1);
+  for (int j = 0; j < ps->nvar; ++j) {
+    fill_f64_kernel<<<grid_for(n, sm), 256, 0, st>>>(ps->var + (size_t)j * ps->cap + off,
+                                                     std::numeric_limits<double>::quiet_NaN(), n);
+    note_launches(1);
+  }
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
+  return PG_OK;
+}
+
 }  // namespace
+
+namespace pg {
+
+// The kernel argument block of kernel k on field set fs: parameters given as
+// NaN, and those of the worked example's behaviours, come from the field
+// set's constants ("Kh", "w_sink", "dwelling_depth", "max_age").
+pg_status resolve_kernel(const pg_kernel *k, const pg_fieldset *fs, uint64_t seed, KernArgs &a) {
+  auto constant = [&](const char *name, double &v) -> bool {
+    auto it = fs->constants.find(name);
+    if (it == fs->constants.end()) {
+      set_error("the kernel needs the field set constant \"%s\"", name);
+      return false;
+    }
+    v = it->second;
+    return true;
+  };
+  a = KernArgs();
+  a.scheme = k->scheme; a.beh = k->beh;
+  a.kh = k->kh; a.w_sink = k->w_sink;
+  if ((k->beh & PG_BROWNIAN) && std::isnan(a.kh) && !constant("Kh", a.kh)) return PG_ERR_STATE;
+  if ((k->beh & (PG_SINK | PG_SETTLE)) && std::isnan(a.w_sink) && !constant("w_sink", a.w_sink))
+    return PG_ERR_STATE;
+  if (std::isnan(a.kh)) a.kh = 0.0;
+  if (std::isnan(a.w_sink)) a.w_sink = 0.0;
+  if ((k->beh & PG_SETTLE) && !constant("dwelling_depth", a.dwell)) return PG_ERR_STATE;
+  if ((k->beh & PG_AGE) && !constant("max_age", a.max_age)) return PG_ERR_STATE;
+  if (!(a.kh >= 0.0)) {
+    set_error("Kh must be >= 0");
+    return PG_ERR_ARG;
+  }
+  a.seed = seed; a.deg_m = 1852.0 * 60.0;
+  a.deg_m_f = (float)a.deg_m; a.inv_deg_m_f = (float)(1.0 / a.deg_m);
+  a.kh_f = (float)a.kh; a.w_sink_f = (float)a.w_sink;
+  a.dwell_f = (float)a.dwell;
+  return PG_OK;
+}
+
+}  // namespace pg
 
 // ======================================================================== ABI
 
@@ -492,23 +581,30 @@ pg_status pg_fieldset_set_times(pg_fieldset *fs, int nt, const double *times, do
   double *d_times = nullptr;
   const void **d_tab = nullptr;
   float *d_scales = nullptr;
+  const void **d_ttab = nullptr;
   cudaError_t e = dev_alloc((void **)&d_times, nt * 8);
   if (e == cudaSuccess) e = dev_alloc((void **)&d_tab, nt * sizeof(void *));
   if (e == cudaSuccess) e = dev_alloc((void **)&d_scales, (size_t)nt * fs->nfields * 4);
+  if (e == cudaSuccess) e = dev_alloc((void **)&d_ttab, 2 * (size_t)nt * sizeof(void *));
   std::vector<float> ones((size_t)nt * fs->nfields, 1.0f);
   std::vector<const void *> nulls((size_t)nt, nullptr);
   if (e == cudaSuccess) e = cudaMemcpy(d_times, times, nt * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_tab, nulls.data(), nt * sizeof(void *), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_scales, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice);
+  std::vector<const void *> tnulls(2 * (size_t)nt, nullptr);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(d_ttab, tnulls.data(), tnulls.size() * sizeof(void *), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
-    dev_free(d_times); dev_free(d_tab); dev_free(d_scales);
+    dev_free(d_times); dev_free(d_tab); dev_free(d_scales); dev_free(d_ttab);
     cudaGetLastError();
     set_error("allocation for %d snapshots failed: %s", nt, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? PG_ERR_NOMEM : PG_ERR_CUDA;
   }
   free_resident(fs);
-  dev_free(fs->d_times); dev_free(fs->d_tab); dev_free(fs->d_scales);
-  fs->d_times = d_times; fs->d_tab = d_tab; fs->d_scales = d_scales;
+  free_tracers(fs);
+  dev_free(fs->d_times); dev_free(fs->d_tab); dev_free(fs->d_scales); dev_free(fs->d_ttab);
+  fs->d_times = d_times; fs->d_tab = d_tab; fs->d_scales = d_scales; fs->d_ttab = d_ttab;
+  fs->tr_slabs.assign(2 * (size_t)nt, nullptr);
   fs->nt = nt;
   fs->times.assign(times, times + nt);
   fs->period = period;
@@ -611,12 +707,21 @@ pg_status pg_fieldset_stream(pg_fieldset *fs, const void *const *ptrs, pg_snapsh
   return PG_OK;
 }
 
+pg_status pg_fieldset_set_ring(pg_fieldset *fs, int slots) {
+  clear_error();
+  ARG(fs, "field set must not be NULL");
+  ARG(slots >= 4 && slots <= 64, "the ring holds 4 to 64 snapshots");
+  ARG(!fs->streaming, "set the ring size before pg_fieldset_stream");
+  fs->slot.assign((size_t)slots, Slot());
+  return PG_OK;
+}
+
 pg_status pg_fieldset_device_bytes(const pg_fieldset *fs, size_t *bytes) {
   clear_error();
   ARG(fs && bytes, "arguments must not be NULL");
   size_t b = 0;
   for (void *p : fs->slabs) b += p ? fs->slab_bytes : 0;
-  if (fs->streaming) b += 4 * fs->slab_bytes;
+  if (fs->streaming) b += fs->slot.size() * fs->slab_bytes;
   *bytes = b;
   return PG_OK;
 }
@@ -639,14 +744,110 @@ pg_status pg_fieldset_get_scale(const pg_fieldset *fs, int s, int f, float *scal
   return PG_OK;
 }
 
+pg_status pg_fieldset_add_constant(pg_fieldset *fs, const char *name, double value) {
+  clear_error();
+  ARG(fs && name && name[0], "field set and a non-empty name are needed");
+  ARG(std::isfinite(value), "constants must be finite");
+  fs->constants[name] = value;
+  return PG_OK;
+}
+
+pg_status pg_fieldset_get_constant(const pg_fieldset *fs, const char *name, double *value) {
+  clear_error();
+  ARG(fs && name && value, "arguments must not be NULL");
+  auto it = fs->constants.find(name);
+  if (it == fs->constants.end()) {
+    set_error("the field set has no constant \"%s\"", name);
+    return PG_ERR_ARG;
+  }
+  *value = it->second;
+  return PG_OK;
+}
+
+pg_status pg_fieldset_set_interp(pg_fieldset *fs, int method) {
+  clear_error();
+  ARG(fs, "field set must not be NULL");
+  ARG(method == PG_LINEAR || method == PG_NEAREST, "method must be PG_LINEAR or PG_NEAREST");
+  fs->interp = method;
+  return PG_OK;
+}
+
+pg_status pg_fieldset_add_scalar(pg_fieldset *fs, const char *name, int method, int *index) {
+  clear_error();
+  ARG(fs && name && name[0], "field set and a non-empty name are needed");
+  ARG(method == PG_LINEAR || method == PG_NEAREST, "method must be PG_LINEAR or PG_NEAREST");
+  ARG(fs->nt > 0, "set the snapshot times first");
+  if (fs->ntr >= 2) {
+    set_error("a field set holds at most two scalar fields");
+    return PG_ERR_UNSUPPORTED;
+  }
+  const int q = fs->ntr;
+  fs->tr_name[q] = name;
+  fs->tr_interp[q] = method;
+  fs->ntr = q + 1;
+  if (index) *index = q;
+  return PG_OK;
+}
+
+pg_status pg_fieldset_load_scalar(pg_fieldset *fs, int index, int s, const void *data,
+                                  int src_dtype, void *stream) {
+  clear_error();
+  ARG(fs && data, "field set and data must not be NULL");
+  ARG(index >= 0 && index < fs->ntr, "no scalar field of that index");
+  ARG(s >= 0 && s < fs->nt, "snapshot index out of range");
+  ARG(src_dtype == PG_F64 || src_dtype == PG_F32, "src_dtype must be PG_F64 or PG_F32");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t el = fs->storage == PG_F64 ? 8 : 4;
+  void *&slab = fs->tr_slabs[(size_t)index * fs->nt + s];
+  void *fresh = nullptr;
+  if (!slab) CU(dev_alloc(&fresh, fs->nodes * el));
+  void *dst = slab ? slab : fresh;
+  const size_t src_el = src_dtype == PG_F64 ? 8 : 4;
+  cudaError_t e = cudaSuccess;
+  if (src_el == el) {
+    e = cudaMemcpyAsync(dst, data, fs->nodes * el, cudaMemcpyDefault, st);
+  } else {
+    // convert on the host side of the copy: FP64 source to FP32 storage, or
+    // FP32 source to FP64 storage (exact)
+    void *tmp = nullptr;
+    e = dev_alloc(&tmp, fs->nodes * src_el);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, data, fs->nodes * src_el, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) {
+      if (src_el == 8) f64_to_f32_kernel<<<grid_for((int64_t)fs->nodes, fs->sm_count), 256, 0, st>>>(
+          (const double *)tmp, (float *)dst, (int64_t)fs->nodes);
+      else f32_to_f64_kernel<<<grid_for((int64_t)fs->nodes, fs->sm_count), 256, 0, st>>>(
+          (const float *)tmp, (double *)dst, (int64_t)fs->nodes);
+      note_launches(1);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dev_free(tmp);
+  }
+  const void *entry = dst;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(fs->d_ttab + (size_t)index * fs->nt + s, &entry, sizeof(void *),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    dev_free(fresh);
+    cudaGetLastError();
+    set_error("loading scalar field %d, snapshot %d failed: %s", index, s, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PG_ERR_NOMEM : PG_ERR_CUDA;
+  }
+  slab = dst;
+  return PG_OK;
+}
+
 pg_status pg_fieldset_destroy(pg_fieldset *fs) {
   clear_error();
   if (!fs) return PG_OK;
   cudaDeviceSynchronize();
   free_streaming(fs);
   free_resident(fs);
+  free_tracers(fs);
   dev_free(fs->d_axes64); dev_free(fs->d_axes32); dev_free(fs->d_amax);
   dev_free(fs->d_times); dev_free(fs->d_tab); dev_free(fs->d_scales); dev_free(fs->d_stage);
+  dev_free(fs->d_ttab);
   delete fs;
   return PG_OK;
 }
@@ -656,9 +857,10 @@ pg_status pg_kernel_create(int scheme, unsigned behaviours, double kh, double w_
   clear_error();
   ARG(out, "out must not be NULL");
   ARG(scheme == PG_EULER || scheme == PG_RK4, "scheme must be PG_EULER or PG_RK4");
-  ARG((behaviours & ~(PG_BROWNIAN | PG_SINK)) == 0, "unknown behaviour bits");
-  ARG(std::isfinite(kh) && kh >= 0.0, "kh must be finite and >= 0");
-  ARG(std::isfinite(w_sink), "w_sink must be finite");
+  ARG((behaviours & ~(PG_BROWNIAN | PG_SINK | PG_SETTLE | PG_AGE | PG_SAMPLE)) == 0,
+      "unknown behaviour bits");
+  ARG(std::isnan(kh) || (std::isfinite(kh) && kh >= 0.0), "kh must be NaN, or finite and >= 0");
+  ARG(std::isnan(w_sink) || std::isfinite(w_sink), "w_sink must be NaN or finite");
   auto *k = new pg_kernel();
   k->scheme = scheme; k->beh = behaviours; k->kh = kh; k->w_sink = w_sink;
   *out = k;
@@ -754,8 +956,9 @@ pg_status pg_pset_create(pg_fieldset *fs, int64_t n, const double *lon, const do
   }
   auto *ps = new pg_pset();
   ps->fs = fs; ps->pos = pos; ps->seed = seed;
+  ps->nvar = fs->ntr;
   PsetArrays A;
-  pg_status r = alloc_arrays(A, pos, n);
+  pg_status r = alloc_arrays(A, pos, n, ps->nvar);
   if (r) { delete ps; return r; }
   set_arrays(ps, A);
   ps->cap = std::max<int64_t>(n, 1);
@@ -771,6 +974,7 @@ pg_status pg_pset_create(pg_fieldset *fs, int64_t n, const double *lon, const do
   }
   double tmin = t0, tmax = t0;
   if (n > 0) r = fill_particles(ps, 0, n, lon, lat, depth, time, t0, ids, id_base, 0, tmin, tmax);
+  if (!r) r = init_variables(ps, 0, n, 0);
   if (r) {
     A.free_all(); dev_free(ps->d_counter); dev_free(ps->d_err);
     delete ps;
@@ -794,7 +998,7 @@ pg_status pg_pset_add(pg_pset *ps, int64_t n, const double *lon, const double *l
   if (ps->n + n > ps->cap) {
     const int64_t cap = std::max<int64_t>(ps->n + n, ps->cap + ps->cap / 2);
     PsetArrays B;
-    pg_status r = alloc_arrays(B, ps->pos, cap);
+    pg_status r = alloc_arrays(B, ps->pos, cap, ps->nvar);
     if (r) return r;
     PsetArrays A = arrays_of(ps);
     const size_t el = pos_elem(ps->pos);
@@ -811,6 +1015,9 @@ pg_status pg_pset_add(pg_pset *ps, int64_t n, const double *lon, const double *l
     }
     cp(B.time, A.time, m * 8); cp(B.id, A.id, m * 8); cp(B.step, A.step, m * 4);
     cp(B.status, A.status, m);
+    cp(B.age, A.age, m * 8);
+    for (int j = 0; j < ps->nvar; ++j)
+      cp(B.var + (size_t)j * cap, A.var + (size_t)j * ps->cap, m * 8);
     if (e != cudaSuccess) {
       B.free_all();
       set_error("grow copy failed: %s", cudaGetErrorString(e));
@@ -822,6 +1029,7 @@ pg_status pg_pset_add(pg_pset *ps, int64_t n, const double *lon, const double *l
   }
   double tmin, tmax;
   pg_status r = fill_particles(ps, ps->n, n, lon, lat, depth, time, t0, ids, id_base, 0, tmin, tmax);
+  if (!r) r = init_variables(ps, ps->n, n, 0);
   if (r) return r;
   if (ps->n == 0) { ps->t_min = tmin; ps->t_max = tmax; }
   else { ps->t_min = std::min(ps->t_min, tmin); ps->t_max = std::max(ps->t_max, tmax); }
@@ -905,6 +1113,21 @@ pg_status pg_pset_get(const pg_pset *ps, double *lon, double *lat, double *depth
   return r;
 }
 
+pg_status pg_pset_get_variables(const pg_pset *ps, double *age, double *vars, void *stream) {
+  clear_error();
+  ARG(ps, "particle set must not be NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = ps->n;
+  if (n == 0) return PG_OK;
+  if (age) CU(cudaMemcpyAsync(age, ps->age, n * 8, cudaMemcpyDefault, st));
+  if (vars)
+    for (int j = 0; j < ps->nvar; ++j)
+      CU(cudaMemcpyAsync(vars + (size_t)j * n, ps->var + (size_t)j * ps->cap, n * 8,
+                         cudaMemcpyDefault, st));
+  CU(cudaStreamSynchronize(st));
+  return PG_OK;
+}
+
 pg_status pg_pset_set_tune(pg_pset *ps, const pg_tune *tune) {
   clear_error();
   ARG(ps && tune, "arguments must not be NULL");
@@ -933,27 +1156,54 @@ pg_status pg_pset_moments(const pg_pset *ps, double out[7], void *stream) {
   return PG_OK;
 }
 
-// Output: copy the state to the host, widen to FP64 and call the hook.
-static pg_status emit_output(pg_pset *ps, double t, pg_output_cb out, void *user,
-                             cudaStream_t st) {
-  const int64_t n = ps->n;
-  std::vector<double> lon(n), lat(n), dep(n);
-  std::vector<uint64_t> ids(n);
-  std::vector<uint8_t> stat(n);
-  pg_status r = pg_pset_get(ps, lon.data(), lat.data(), dep.data(), nullptr, ids.data(), nullptr,
-                            stat.data(), st);
-  if (r) return r;
-  if (out(user, t, n, ids.data(), lon.data(), lat.data(), dep.data(), stat.data()) != 0) {
+// Deliver the output waiting in ring slot k to the caller's hook.
+static pg_status deliver_output(pg_pset *ps, int k, pg_output_cb out, pg_record_cb rec,
+                                void *user) {
+  OutputView hv;
+  double t = 0.0;
+  CU(ps->out->wait(k, hv, t));
+  ps->out->slot[k].pending = false;
+  const int64_t n = (int64_t)*hv.count;
+  int r;
+  if (rec) {
+    pg_record R;
+    R.time = t; R.n = n; R.nvar = ps->out->nvar; R.var_stride = ps->out->cap;
+    R.id = hv.id; R.lon = hv.lon; R.lat = hv.lat; R.depth = hv.depth; R.status = hv.status;
+    R.age = hv.age; R.vars = hv.vars;
+    r = rec(user, &R);
+  } else {
+    r = out(user, t, n, hv.id, hv.lon, hv.lat, hv.depth, hv.status);
+  }
+  if (r != 0) {
     set_error("output callback failed at t = %g", t);
     return PG_ERR_CALLBACK;
   }
   return PG_OK;
 }
 
+static pg_status execute_impl(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
+                              double output_dt, pg_output_cb out, pg_record_cb rec, int indexed,
+                              void *user, void *stream, int64_t *steps_done);
+
 pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
                      double output_dt, pg_output_cb out, void *user, void *stream,
                      int64_t *steps_done) {
   clear_error();
+  return execute_impl(ps, k, runtime, dt, output_dt, out, nullptr, 0, user, stream, steps_done);
+}
+
+pg_status pg_execute_records(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
+                             double output_dt, int indexed, pg_record_cb rec, void *user,
+                             void *stream, int64_t *steps_done) {
+  clear_error();
+  ARG(indexed == 0 || indexed == 1, "indexed must be 0 or 1");
+  return execute_impl(ps, k, runtime, dt, output_dt, nullptr, rec, indexed, user, stream,
+                      steps_done);
+}
+
+static pg_status execute_impl(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
+                              double output_dt, pg_output_cb out, pg_record_cb rec, int indexed,
+                              void *user, void *stream, int64_t *steps_done) {
   ARG(ps && k, "particle set and kernel must not be NULL");
   ARG(std::isfinite(runtime) && runtime >= 0.0, "runtime must be finite and >= 0");
   ARG(std::isfinite(dt) && dt != 0.0, "dt must be finite and non-zero");
@@ -991,17 +1241,58 @@ pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
     }
   }
   StepArgs a;
+  {
+    pg_status r = resolve_kernel(k, fs, ps->seed, a.k);
+    if (r) return r;
+  }
+  const bool ext = (k->beh & (PG_SETTLE | PG_AGE | PG_SAMPLE)) || fs->interp != PG_LINEAR;
+  if (ext && ps->pos == PG_POS_CELL) {
+    set_error("the settle, age and sample behaviours and nearest-neighbour interpolation need "
+              "lon/lat/depth positions");
+    return PG_ERR_UNSUPPORTED;
+  }
+  if (ext && ps->pos == PG_POS_F32 && fs->storage != PG_F32) {
+    set_error("the settle, age and sample behaviours and nearest-neighbour interpolation need "
+              "FP32 or FP64 field storage");
+    return PG_ERR_UNSUPPORTED;
+  }
+  if (k->beh & PG_SAMPLE) {
+    if (fs->ntr == 0 || ps->nvar != fs->ntr) {
+      set_error("the sample behaviour needs scalar fields, added before the particle set");
+      return PG_ERR_STATE;
+    }
+    if (fs->streaming) {
+      set_error("scalar fields are sampled from resident snapshots only");
+      return PG_ERR_UNSUPPORTED;
+    }
+    for (size_t q = 0; q < (size_t)fs->ntr * fs->nt; ++q)
+      if (!fs->tr_slabs[q]) {
+        set_error("snapshot %d of scalar field %d has not been loaded", (int)(q % fs->nt),
+                  (int)(q / fs->nt));
+        return PG_ERR_STATE;
+      }
+  }
   a.g = grid_args(fs);
   a.f.nt = fs->nt; a.f.nf = fs->nfields; a.f.times = fs->d_times; a.f.period = fs->period;
   a.f.tab = fs->d_tab;
   a.f.scales = (fs->storage == PG_F16S || fs->storage == PG_BF16S) ? fs->d_scales : nullptr;
-  a.k.scheme = k->scheme; a.k.beh = k->beh; a.k.kh = k->kh; a.k.w_sink = k->w_sink;
-  a.k.seed = ps->seed; a.k.deg_m = 1852.0 * 60.0;
-  a.k.deg_m_f = (float)a.k.deg_m; a.k.inv_deg_m_f = (float)(1.0 / a.k.deg_m);
-  a.k.kh_f = (float)k->kh; a.k.w_sink_f = (float)k->w_sink;
+  a.f.nearest = fs->interp;
+  a.f.ntr = (k->beh & PG_SAMPLE) ? fs->ntr : 0;
+  a.f.ttab = fs->d_ttab;
+  a.f.tnearest[0] = fs->tr_interp[0]; a.f.tnearest[1] = fs->tr_interp[1];
   a.dt = dt; a.t_end = t_end;
   a.steps_done = ps->d_counter;
   a.err = ps->d_err;
+  // everything the time loop allocates is allocated before its first launch,
+  // so a failed allocation leaves the particles as they were
+  if (ps->tune.resort_steps > 0) CU(prepare_resort(ps));
+  const bool want_out = output_dt > 0.0 && (out != nullptr || rec != nullptr);
+  if (want_out) {
+    if (!ps->out) ps->out = new OutputRing();
+    CU(ps->out->prepare(ps->cap, ps->nvar));
+  }
+  double t_prev_out = t_begin;
+  int pending_out = -1;              // ring slot whose output awaits delivery
   CU(cudaMemsetAsync(ps->d_counter, 0, 8, st));
   CU(cudaMemsetAsync(ps->d_err, 0, 4, st));
 
@@ -1030,15 +1321,17 @@ pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
       pg_status r = ensure_slots(fs, need, -1, st);
       if (r) return r;
     } else if (fs->streaming) {
-      // end the chunk at the next snapshot time; make resident the snapshots
-      // bracketing every stage time a step starting in the chunk can reach,
-      // and start uploading the one after them
+      // end the chunk at most B = slots - 4 snapshot times after the next
+      // one (B = 0: at the next snapshot time); make resident the snapshots
+      // bracketing every stage time a step starting in the chunk can reach
+      // (B + 3 of them), and start uploading the one after them
       const long long m = snap_counter(fs, tc);
+      const long long B = (long long)fs->slot.size() - 4;
       if (sgn > 0) {
-        clip(snap_time(fs, m + 1));
+        clip(snap_time(fs, m + 1 + B));
       } else {
-        const double b = snap_time(fs, m);
-        clip(b < tc ? b : snap_time(fs, m - 1));
+        const double b = snap_time(fs, m - B);
+        clip(b < tc ? b : snap_time(fs, m - 1 - B));
       }
       const double adt = std::fabs(dt);
       const double lo_t = sgn > 0 ? tc : std::max(tn - adt, t_end);
@@ -1058,6 +1351,7 @@ pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
     a.p.n = n_active;
     a.p.x = ps->x; a.p.y = ps->y; a.p.z = ps->z;
     a.p.time = ps->time; a.p.id = ps->id; a.p.step = ps->step; a.p.status = ps->status;
+    a.p.age = ps->age; a.p.var = ps->var; a.p.vstride = ps->cap;
     a.t_stop = tn;
     if (ps->timing) {
       if (ps->ev_used + 2 > ps->ev.size()) {
@@ -1083,15 +1377,31 @@ pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
       CU(launch_resort(ps, st, &n_active));
       next_sort = tc + sgn * resort_len;
     }
-    if (out && output_dt > 0.0 && (tc == next_out || tc == t_end)) {
-      pg_status r = emit_output(ps, tc, out, user, st);
-      if (r) return r;
+    if (want_out && (tc == next_out || tc == t_end)) {
+      // pack this output and start its copy; then hand the previous one to
+      // the caller while the GPU goes on
+      CU(ps->out->enqueue(ps, tc, t_prev_out, sgn, indexed, st));
+      const int just = ps->out->next ^ 1;
+      if (pending_out >= 0) {
+        pg_status r = deliver_output(ps, pending_out, out, rec, user);
+        if (r) {
+          cudaStreamSynchronize(st);
+          ps->out->slot[just].pending = false;
+          return r;
+        }
+      }
+      pending_out = just;
+      t_prev_out = tc;
     }
     if (tc == next_out) next_out = tc + sgn * output_dt;
     if (++guard > 100000000) {
       set_error("time loop made no progress");
       return PG_ERR_STATE;
     }
+  }
+  if (pending_out >= 0) {
+    pg_status r = deliver_output(ps, pending_out, out, rec, user);
+    if (r) return r;
   }
   unsigned long long done = 0;
   int err = 0;
@@ -1143,7 +1453,7 @@ pg_status pg_pset_save(const pg_pset *ps, const char *path) {
   ARG(ps && path, "arguments must not be NULL");
   const int64_t n = ps->n;
   // raw array bytes keep FP32 and cell-form state bit for bit
-  const auto arrays = state_arrays(arrays_of(ps), ps->pos);
+  const auto arrays = state_arrays(arrays_of(ps), ps->pos, ps->nvar, ps->cap);
   std::vector<std::vector<char>> host(arrays.size());
   for (size_t q = 0; q < arrays.size(); ++q) {
     host[q].resize((size_t)n * arrays[q].second);
@@ -1154,9 +1464,10 @@ pg_status pg_pset_save(const pg_pset *ps, const char *path) {
     set_error("cannot open %s for writing", path);
     return PG_ERR_ARG;
   }
-  const char magic[8] = {'P', 'G', 'P', 'S', 'E', 'T', '0', '2'};
-  const int32_t pos = ps->pos;
+  const char magic[8] = {'P', 'G', 'P', 'S', 'E', 'T', '0', '3'};
+  const int32_t pos = ps->pos, nvar = ps->nvar;
   bool ok = fwrite(magic, 8, 1, f) == 1 && fwrite(&pos, 4, 1, f) == 1 &&
+            fwrite(&nvar, 4, 1, f) == 1 &&
             fwrite(&n, 8, 1, f) == 1 && fwrite(&ps->seed, 8, 1, f) == 1 &&
             fwrite(&ps->t_min, 8, 1, f) == 1 && fwrite(&ps->t_max, 8, 1, f) == 1;
   for (size_t q = 0; ok && q < host.size(); ++q)
@@ -1178,18 +1489,19 @@ pg_status pg_pset_restore(pg_fieldset *fs, const char *path, pg_pset **out) {
     return PG_ERR_ARG;
   }
   char magic[8];
-  int32_t pos = 0;
+  int32_t pos = 0, nvar = 0;
   int64_t n = 0;
   uint64_t seed = 0;
   double tmin = 0, tmax = 0;
-  bool ok = fread(magic, 8, 1, f) == 1 && memcmp(magic, "PGPSET02", 8) == 0 &&
-            fread(&pos, 4, 1, f) == 1 && fread(&n, 8, 1, f) == 1 && fread(&seed, 8, 1, f) == 1 &&
+  bool ok = fread(magic, 8, 1, f) == 1 && memcmp(magic, "PGPSET03", 8) == 0 &&
+            fread(&pos, 4, 1, f) == 1 && fread(&nvar, 4, 1, f) == 1 && nvar >= 0 && nvar <= 2 &&
+            fread(&n, 8, 1, f) == 1 && fread(&seed, 8, 1, f) == 1 &&
             fread(&tmin, 8, 1, f) == 1 && fread(&tmax, 8, 1, f) == 1 &&
             (pos == PG_POS_F64 || pos == PG_POS_F32 || pos == PG_POS_CELL) && n >= 0 &&
             n < ((int64_t)1 << 40);
   std::vector<std::vector<char>> host;
   if (ok) {
-    const auto sizes = state_arrays(PsetArrays(), pos);
+    const auto sizes = state_arrays(PsetArrays(), pos, nvar, n);
     host.resize(sizes.size());
     for (size_t q = 0; ok && q < sizes.size(); ++q) {
       host[q].resize((size_t)n * sizes[q].second);
@@ -1201,6 +1513,11 @@ pg_status pg_pset_restore(pg_fieldset *fs, const char *path, pg_pset **out) {
     set_error("%s is not a particle-set checkpoint", path);
     return PG_ERR_ARG;
   }
+  if (nvar != fs->ntr) {
+    set_error("checkpoint %s has %d sampled variables, the field set %d scalar fields", path,
+              (int)nvar, fs->ntr);
+    return PG_ERR_ARG;
+  }
   // create an empty set of the right form, then fill it raw
   pg_pset *ps = nullptr;
   pg_status r = pg_pset_create(fs, 0, nullptr, nullptr, nullptr, nullptr, tmin, nullptr, 0, pos,
@@ -1208,9 +1525,9 @@ pg_status pg_pset_restore(pg_fieldset *fs, const char *path, pg_pset **out) {
   if (r) return r;
   if (n) {
     PsetArrays B;
-    r = alloc_arrays(B, pos, n);
+    r = alloc_arrays(B, pos, n, nvar);
     if (r) { pg_pset_destroy(ps); return r; }
-    const auto arrays = state_arrays(B, pos);
+    const auto arrays = state_arrays(B, pos, nvar, n);
     cudaError_t e = cudaSuccess;
     for (size_t q = 0; e == cudaSuccess && q < arrays.size(); ++q)
       e = cudaMemcpy(arrays[q].first, host[q].data(), host[q].size(), cudaMemcpyHostToDevice);
@@ -1241,6 +1558,7 @@ pg_status pg_pset_destroy(pg_pset *ps) {
   dev_free(ps->sort_scratch);
   dev_free(ps->diag_scratch);
   for (cudaEvent_t ev : ps->ev) cudaEventDestroy(ev);
+  delete ps->out;
   delete ps;
   return PG_OK;
 }

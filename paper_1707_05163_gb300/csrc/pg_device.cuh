@@ -44,6 +44,11 @@ struct FieldArgs {
   double period;             // > 0: time-periodic
   const void *const *tab;    // [nt] device pointers to interleaved slabs (null if absent)
   const float *scales;       // [nt * nf] FP32 scales (quantised storage) or null
+  int nearest = 0;           // velocities: 0 linear, 1 nearest node in space
+  int ntr = 0;               // scalar fields (tracers) sampled into particle variables
+  const void *const *ttab = nullptr;   // [ntr * nt] planar tracer slabs (double for FP64
+                                       // storage, float otherwise)
+  int tnearest[2] = {0, 0};  // per tracer: 0 linear, 1 nearest node
 };
 
 struct KernArgs {
@@ -53,7 +58,14 @@ struct KernArgs {
   uint64_t seed;
   double deg_m;              // metres per degree
   float deg_m_f, inv_deg_m_f, kh_f, w_sink_f;   // FP32 copies for the FP32 path
+  double dwell = 0.0, max_age = 0.0;   // settle: dwelling depth (m); age: deletion age (s)
+  float dwell_f = 0.f;
 };
+
+// Behaviour bits of the worked example (Sect. 3), beside Brownian (1) and
+// sinking (2); and the status of a particle an age behaviour deleted.
+enum : unsigned { BEH_SETTLE = 4u, BEH_AGE = 8u, BEH_SAMPLE = 16u };
+enum : int { STATUS_DELETED = 4 };
 
 struct PartArgs {
   int64_t n;
@@ -64,6 +76,9 @@ struct PartArgs {
   const uint64_t *id;
   uint32_t *step;
   uint8_t *status;
+  double *age = nullptr;     // [n] seconds of age (age behaviour)
+  double *var = nullptr;     // [ntr][vstride] sampled variables (sample behaviour)
+  int64_t vstride = 0;
 };
 
 // Mesh geometry of a kernel instantiation: runtime (GEO_ANY, the FP64 path)

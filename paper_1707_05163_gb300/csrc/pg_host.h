@@ -3,7 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -40,19 +42,69 @@ struct PsetArrays {
   uint64_t *id = nullptr;
   uint32_t *step = nullptr;
   uint8_t *status = nullptr;
+  double *age = nullptr;      // [cap]
+  double *var = nullptr;      // [nvar][cap] sampled variables
   void free_all() {
-    void *ps[] = {x, y, z, ci, cj, ck, fx, fy, fz, time, id, step, status};
+    void *ps[] = {x, y, z, ci, cj, ck, fx, fy, fz, time, id, step, status, age, var};
     for (void *p : ps) dev_free(p);
     *this = PsetArrays();
   }
 };
 
-pg_status alloc_arrays(PsetArrays &A, int pos, int64_t cap);
+// Allocate the arrays of `cap` particles with `nvar` sampled variables.
+pg_status alloc_arrays(PsetArrays &A, int pos, int64_t cap, int nvar);
+
+// Arrays of one output slot (device or pinned host), cap rows each.
+struct OutputView {
+  uint64_t *id = nullptr;
+  double *lon = nullptr, *lat = nullptr, *depth = nullptr, *age = nullptr;
+  double *vars = nullptr;       // [nvar][cap]
+  uint8_t *status = nullptr;
+  uint32_t *count = nullptr;    // rows written
+};
+
+struct OutputSlot {
+  void *d = nullptr;            // device slot
+  void *h = nullptr;            // pinned host copy
+  cudaEvent_t packed = nullptr, copied = nullptr;
+  double time = 0.0;
+  bool pending = false;
+};
+
+// Two-slot pinned output ring of a particle set (output.cu).
+struct OutputRing {
+  int64_t cap = 0;
+  int nvar = 0;
+  OutputSlot slot[2];
+  uint32_t *d_tiles = nullptr;  // tile counts and offsets of the compaction
+  cudaStream_t cs = nullptr;    // the copy stream
+  int next = 0;                 // slot of the next output
+  ~OutputRing();
+  void release();
+  cudaError_t prepare(int64_t need_cap, int need_nvar);
+  // pack the output at time t into slot `next` on `st` and copy it to the
+  // host on the copy stream; indexed: rows of alive particles and of those
+  // deleted at or after t_prev (direction sgn)
+  cudaError_t enqueue(const pg_pset *ps, double t, double t_prev, double sgn, int indexed,
+                      cudaStream_t st);
+  // wait for slot k's copy; host views of its arrays and its time
+  cudaError_t wait(int k, OutputView &hv, double &t);
+  static OutputView view(const void *base, int64_t rows_cap, int nv);
+};
 
 }  // namespace pg
 
 struct pg_fieldset {
   int device = 0;
+  // constants carried by the field set (Sect. 3), read by the behaviours
+  std::map<std::string, double> constants;
+  int interp = 0;               // velocities: 0 linear, 1 nearest
+  // scalar fields (tracers) sampled into particle variables, resident only
+  int ntr = 0;
+  std::string tr_name[2];
+  int tr_interp[2] = {0, 0};
+  std::vector<void *> tr_slabs; // [2 * nt] planar slabs (null until loaded)
+  const void **d_ttab = nullptr;// device copy of tr_slabs
   int sm_count = 0;
   int nx = 0, ny = 0, nz = 0, mesh = 0, periodic = 0, nfields = 0, storage = 0;
   std::vector<double> lon, lat, depth;
@@ -81,7 +133,7 @@ struct pg_fieldset {
   pg_snapshot_cb cb = nullptr;
   void *cb_user = nullptr;
   int src_dtype = PG_F32;
-  pg::Slot slot[4];
+  std::vector<pg::Slot> slot = std::vector<pg::Slot>(4);   // the ring (>= 4 slots)
   void *h_pinned = nullptr;     // pinned staging for callback sources
   cudaStream_t side = nullptr;
   cudaEvent_t stage_free = nullptr;
@@ -92,7 +144,7 @@ struct pg_fieldset {
 struct pg_kernel {
   int scheme = PG_RK4;
   unsigned beh = 0;
-  double kh = 0.0, w_sink = 0.0;
+  double kh = 0.0, w_sink = 0.0;   // NaN: the field set's constant of that name
 };
 
 struct pg_pset {
@@ -107,6 +159,9 @@ struct pg_pset {
   uint64_t *id = nullptr;
   uint32_t *step = nullptr;
   uint8_t *status = nullptr;
+  double *age = nullptr;               // [cap] age in seconds (age behaviour)
+  double *var = nullptr;               // [nvar][cap] sampled variables
+  int nvar = 0;                        // the field set's scalar fields at creation
   double t_min = 0.0, t_max = 0.0;     // range of particle times
   pg_tune tune{256, 0, 64};
   unsigned long long *d_counter = nullptr;
@@ -117,6 +172,8 @@ struct pg_pset {
   void *sort_scratch = nullptr;
   size_t sort_scratch_bytes = 0;
   double *diag_scratch = nullptr;
+  // trajectory output ring, on first use
+  pg::OutputRing *out = nullptr;
   // optional CUDA-event timing of the advection launches
   bool timing = false;
   std::vector<cudaEvent_t> ev;        // pairs (start, stop) per launch
@@ -147,6 +204,18 @@ cudaError_t launch_from_cell(const GridArgs &g, const int32_t *ci, const int32_t
 
 // Grid argument block of a field set (defined in capi.cu).
 GridArgs grid_args_of(const pg_fieldset *fs);
+
+// Kernel argument block of a kernel on a field set: NaN parameters and those
+// of the settle and age behaviours from the field set's constants (capi.cu).
+pg_status resolve_kernel(const pg_kernel *k, const pg_fieldset *fs, uint64_t seed, KernArgs &a);
+
+// The device arrays of a particle set, and replacing them (capi.cu).
+PsetArrays pset_arrays(const pg_pset *ps);
+void pset_set_arrays(pg_pset *ps, const PsetArrays &A);
+
+// Advection chunk with the worked example's behaviours or nearest-neighbour
+// interpolation on FP32 positions and FP32 storage (advect_f32_ext.cu).
+cudaError_t launch_advect_plain_ext(const StepArgs &a, int block, cudaStream_t st);
 
 // Element size of one position coordinate for a position form.
 inline size_t pos_elem(int pos) { return pos == PG_POS_F64 ? 8 : 4; }

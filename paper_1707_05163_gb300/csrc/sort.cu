@@ -215,10 +215,13 @@ cudaError_t prepare_resort(pg_pset *ps) {
     if ((e = dev_alloc(&ps->sort_scratch, need)) != cudaSuccess) return e;
     ps->sort_scratch_bytes = need;
   }
-  if (ps->alt_cap < ps->cap) {
+  // the second set has exactly the first one's capacity: the sampled
+  // variables are laid out with the capacity as their stride
+  if (ps->alt_cap != ps->cap) {
     ps->alt.free_all();
     ps->alt_cap = 0;
-    if (alloc_arrays(ps->alt, ps->pos, ps->cap) != PG_OK) return cudaErrorMemoryAllocation;
+    if (alloc_arrays(ps->alt, ps->pos, ps->cap, ps->nvar) != PG_OK)
+      return cudaErrorMemoryAllocation;
     ps->alt_cap = ps->cap;
   }
   return cudaSuccess;
@@ -288,7 +291,11 @@ cudaError_t launch_resort(pg_pset *ps, cudaStream_t st, int64_t *n_alive) {
   gather_kernel<uint64_t><<<gr, 256, 0, st>>>(ps->id, B.id, perm, n);
   gather_kernel<uint32_t><<<gr, 256, 0, st>>>(ps->step, B.step, perm, n);
   gather_kernel<uint8_t><<<gr, 256, 0, st>>>(ps->status, B.status, perm, n);
-  note_launches(ps->pos == PG_POS_CELL ? 11 : 8);
+  gather_kernel<double><<<gr, 256, 0, st>>>(ps->age, B.age, perm, n);
+  for (int j = 0; j < ps->nvar; ++j)
+    gather_kernel<double><<<gr, 256, 0, st>>>(ps->var + (size_t)j * ps->cap,
+                                              B.var + (size_t)j * ps->cap, perm, n);
+  note_launches((ps->pos == PG_POS_CELL ? 11 : 8) + 1 + ps->nvar);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (!n_alive) {
     // fixed-pointer mode: copy the sorted arrays back in place
@@ -303,18 +310,18 @@ cudaError_t launch_resort(pg_pset *ps, cudaStream_t st, int64_t *n_alive) {
     if ((e = cudaMemcpyAsync(ps->time, B.time, (size_t)n * 8, cudaMemcpyDeviceToDevice, st)) ||
         (e = cudaMemcpyAsync(ps->id, B.id, (size_t)n * 8, cudaMemcpyDeviceToDevice, st)) ||
         (e = cudaMemcpyAsync(ps->step, B.step, (size_t)n * 4, cudaMemcpyDeviceToDevice, st)) ||
-        (e = cudaMemcpyAsync(ps->status, B.status, (size_t)n, cudaMemcpyDeviceToDevice, st)))
+        (e = cudaMemcpyAsync(ps->status, B.status, (size_t)n, cudaMemcpyDeviceToDevice, st)) ||
+        (e = cudaMemcpyAsync(ps->age, B.age, (size_t)n * 8, cudaMemcpyDeviceToDevice, st)))
       return e;
+    for (int j = 0; j < ps->nvar; ++j)
+      if ((e = cudaMemcpyAsync(ps->var + (size_t)j * ps->cap, B.var + (size_t)j * ps->cap,
+                               (size_t)n * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return e;
     return cudaSuccess;
   }
   // swap the two array sets
-  PsetArrays A;
-  A.x = ps->x; A.y = ps->y; A.z = ps->z; A.ci = ps->ci; A.cj = ps->cj; A.ck = ps->ck;
-  A.fx = ps->fx; A.fy = ps->fy; A.fz = ps->fz; A.time = ps->time; A.id = ps->id;
-  A.step = ps->step; A.status = ps->status;
-  ps->x = B.x; ps->y = B.y; ps->z = B.z; ps->ci = B.ci; ps->cj = B.cj; ps->ck = B.ck;
-  ps->fx = B.fx; ps->fy = B.fy; ps->fz = B.fz; ps->time = B.time; ps->id = B.id;
-  ps->step = B.step; ps->status = B.status;
+  const PsetArrays A = pset_arrays(ps);
+  pset_set_arrays(ps, B);
   B = A;
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
   *n_alive = n - (int64_t)dead_count;

@@ -375,13 +375,10 @@ pg_status pg_surrogate_run(pg_pset *ps, pg_mlp *net, const pg_kernel *k, int nst
   auto copy_set = [&](pg_pset *dst, const pg_pset *src) -> cudaError_t {
     if (dst->cap < src->n) {
       PsetArrays A;
-      if (alloc_arrays(A, PG_POS_F32, src->n) != PG_OK) return cudaErrorMemoryAllocation;
-      PsetArrays old;
-      old.x = dst->x; old.y = dst->y; old.z = dst->z; old.time = dst->time; old.id = dst->id;
-      old.step = dst->step; old.status = dst->status;
-      old.free_all();
-      dst->x = A.x; dst->y = A.y; dst->z = A.z; dst->time = A.time; dst->id = A.id;
-      dst->step = A.step; dst->status = A.status;
+      if (alloc_arrays(A, PG_POS_F32, src->n, dst->nvar) != PG_OK)
+        return cudaErrorMemoryAllocation;
+      pset_arrays(dst).free_all();
+      pset_set_arrays(dst, A);
       dst->cap = src->n;
     }
     const size_t m = (size_t)src->n;

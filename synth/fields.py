@@ -26,7 +26,7 @@ __all__ = [
     "FLAT", "SPHERICAL", "DAY", "FieldSpec", "GlobalField", "solid_body_rotation",
     "zonal_flow_sphere", "oscillating_flow", "peninsula", "peninsula_psi",
     "stommel_gyre", "stommel_psi", "decaying_eddy", "eddy_trajectory", "zero_field",
-    "uniform_flow", "linear_field", "global_axes",
+    "uniform_flow", "linear_field", "global_axes", "temperature",
 ]
 
 
@@ -351,3 +351,30 @@ def _global_base2d_torch(self, s, device):
 
 
 GlobalField.base2d_torch = _global_base2d_torch
+
+
+def temperature(lon, lat, depth, times, seed=9, period=30 * DAY, noise=0.5):
+    """Seeded synthetic sea temperature (deg C) on a grid, (nt, nz, ny, nx).
+
+    A warm surface that cools towards the poles and with depth, 2 + 26
+    cos^2(lat) exp(-z / 700 m), plus a seasonal-like swing of 1 degree with
+    the given period and seeded random perturbations of rms `noise` (a
+    stand-in for the OGCM temperature the worked example samples).  Flat
+    grids use lat in metres scaled to +-60 degrees.
+    """
+    rng = np.random.default_rng(seed)
+    lon = np.asarray(lon, np.float64)
+    lat = np.asarray(lat, np.float64)
+    depth = np.asarray(depth, np.float64)
+    times = np.atleast_1d(np.asarray(times, np.float64))
+    if np.max(np.abs(lat)) > 90.0:
+        latd = -60.0 + 120.0 * (lat - lat.min()) / max(lat.max() - lat.min(), 1.0)
+    else:
+        latd = lat
+    base = 2.0 + 26.0 * np.cos(np.deg2rad(latd))[None, :, None] ** 2 * \
+        np.exp(-depth / 700.0)[:, None, None]
+    pert = rng.normal(size=(len(depth), len(latd), len(lon))) * noise
+    out = np.empty((len(times), len(depth), len(latd), len(lon)))
+    for s, t in enumerate(times):
+        out[s] = base + np.sin(2 * np.pi * t / period) + pert
+    return out

@@ -1,0 +1,280 @@
+"""The worked example's parts on the GPU against the oracle (Sect. 3: field
+constants, the sampled temperature and age variables, the backward sinking
+phase; Sect. 2.3: nearest-neighbour interpolation).
+
+FP64: on flat meshes both sides carry out the same operations in the same
+order, so positions, ages and sampled values are bit-identical.  FP32 (the
+extended kernel on FP32 storage): equal statuses and step counts, mean
+position error below 1e-3 cell, ages equal, and sampled values within the
+field's change over the position difference.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests.helpers import DAY, cell_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1707_05163_gb300 as pg
+    pg.load()
+    return pg
+
+
+BITS = {"brownian": O.BROWNIAN, "sink": O.SINK, "settle": O.SETTLE, "age": O.AGE,
+        "sample": O.SAMPLE}
+
+
+def _oracle(spec, data, tracers, interp, tracer_interp, lon, lat, dep, t0, dt, T, beh,
+            scheme="rk4", w_sink=0.0, dwell=0.0, max_age=0.0, kh=0.0, seed=0, age0=None):
+    f = O.Field(spec.lon, spec.lat, spec.depth, spec.times, data, spec.mesh, spec.periodic_lon,
+                spec.period, interp=interp, tracers=tracers, tracer_interp=tracer_interp)
+    n = len(lon)
+    st = dict(lon=np.array(lon, np.float64), lat=np.array(lat, np.float64),
+              depth=np.zeros(n) if dep is None else np.array(dep, np.float64),
+              time=np.full(n, t0), ids=np.arange(n, dtype=np.uint64),
+              step=np.zeros(n, np.uint32), status=np.zeros(n, np.uint8))
+    age = np.zeros(n) if age0 is None else age0.copy()
+    var = np.full((len(tracers), n), np.nan)
+    bits = 0
+    for b in beh:
+        bits |= BITS[b]
+    k = O.Kernel(O.RK4 if scheme == "rk4" else O.EULER, bits, kh, w_sink, seed, dwell, max_age)
+    t_end = t0 + np.sign(dt) * T
+    done = O.run(f, k, st["lon"], st["lat"], st["depth"], st["time"], st["ids"], st["step"],
+                 st["status"], dt, t_end, t_end, age=age, variables=var)
+    st["age"], st["vars"], st["steps"] = age, var, done
+    return st
+
+
+def _flat3d(rng, nt=3):
+    """Random smooth-ish 3-D flow on stretched flat axes, time-dependent."""
+    spec, _ = synth.linear_field(rng, nx=12, ny=10, nz=8, nt=nt, nfields=3)
+    spec.data = spec.data * 0.002 + rng.normal(size=spec.data.shape) * 0.002
+    spec.data[:, 2] *= 0.01
+    return spec
+
+
+@pytest.mark.parametrize("scheme", ["rk4", "euler"])
+def test_nearest_fp64_bit_identical(pg, scheme):
+    rng = np.random.default_rng(41)
+    spec = _flat3d(rng)
+    n = 2000
+    lon = rng.uniform(spec.lon[1], spec.lon[-2], n)
+    lat = rng.uniform(spec.lat[1], spec.lat[-2], n)
+    dep = rng.uniform(spec.depth[1], spec.depth[-2], n)
+    T = spec.times[-1] - 1.0
+    o = _oracle(spec, spec.data, (), O.NEAREST, (), lon, lat, dep, 0.0, 900.0, T, (), scheme)
+    fs = pg.FieldSet.from_spec(spec, storage="f64")
+    fs.set_interp("nearest")
+    ps = pg.ParticleSet(fs, lon, lat, dep, pos="f64")
+    steps = ps.execute(pg.Kernel(scheme), T, 900.0)
+    g = ps.get()
+    assert steps == o["steps"]
+    for k in ("lon", "lat", "depth", "status", "step", "time"):
+        np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+    assert (o["status"] != 0).sum() > 20 and (o["status"] == 0).sum() > 500
+
+
+def test_nearest_fp32_on_the_sphere(pg):
+    gf = synth.GlobalField(res_deg=2.0, nz=8, nt=4, seed=23, kmax=20, period=4 * DAY)
+    spec = gf.spec(materialise=True)
+    lon, lat, dep = synth.uniform_particles(3000, 29, (0, 360), (-70, 70), (6.0, 900.0),
+                                            dtype=np.float32)
+    T = DAY
+    o = _oracle(spec, spec.data, (), O.NEAREST, (), lon, lat, dep, 0.0, 1800.0, T, ())
+    fs = pg.FieldSet.from_spec(spec, storage="f32")
+    fs.set_interp("nearest")
+    ps = pg.ParticleSet(fs, lon, lat, dep, pos="f32")
+    assert ps.execute(pg.Kernel("rk4"), T, 1800.0) == o["steps"]
+    g = ps.get()
+    np.testing.assert_array_equal(g["status"], o["status"])
+    e = cell_error(g, o, spec)[o["status"] == 0]
+    # a nearest-node flow jumps at cell midpoints: a few particles take the
+    # other node where FP32 and FP64 positions straddle a midpoint
+    assert np.median(e) < 1e-4 and np.mean(e < 1e-3) > 0.97, (np.median(e), np.mean(e < 1e-3))
+
+
+@pytest.mark.parametrize("tinterp", [O.LINEAR, O.NEAREST])
+def test_sample_and_age_fp64_bit_identical(pg, tinterp):
+    rng = np.random.default_rng(43)
+    spec = _flat3d(rng, nt=4)
+    temp = synth.temperature(spec.lon, spec.lat, spec.depth, spec.times, seed=3)
+    salt = 35.0 + rng.normal(size=temp.shape) * 0.1
+    n = 3000
+    lon = rng.uniform(spec.lon[1], spec.lon[-2], n)
+    lat = rng.uniform(spec.lat[1], spec.lat[-2], n)
+    dep = rng.uniform(spec.depth[1], spec.depth[-2], n)
+    T = spec.times[-1] - 100.0
+    max_age = 0.6 * T
+    o = _oracle(spec, spec.data, (temp, salt), O.LINEAR, (tinterp, O.LINEAR), lon, lat, dep, 0.0,
+                600.0, T, ("age", "sample"), max_age=max_age)
+    fs = pg.FieldSet.from_spec(spec, storage="f64")
+    assert fs.add_scalar("T", "nearest" if tinterp == O.NEAREST else "linear") == 0
+    assert fs.add_scalar("S") == 1
+    for s in range(spec.nt):
+        fs.load_scalar(0, s, temp[s])
+        fs.load_scalar(1, s, salt[s])
+    fs.add_constant("max_age", max_age)
+    ps = pg.ParticleSet(fs, lon, lat, dep, pos="f64")
+    # several launches and a re-sort on the way: variables move with their particles
+    ps.set_tune(block=128, resort_steps=17, chunk_steps=11)
+    assert ps.execute(pg.Kernel("rk4", ("age", "sample")), T, 600.0) == o["steps"]
+    g, v = ps.get(), ps.get_variables()
+    for k in ("lon", "lat", "depth", "status", "step", "time"):
+        np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+    np.testing.assert_array_equal(v["age"], o["age"])
+    np.testing.assert_array_equal(v["vars"], o["vars"])
+    assert (o["status"] == 4).sum() > 1000 and (o["status"] == 1).sum() > 10
+
+
+@pytest.mark.parametrize("pos", ["f64", "f32"])
+def test_backward_two_phase_run_on_the_global_field(pg, pos):
+    """The worked example's experiment (Sect. 3) on the synthetic 3-D global
+    field: particles released at 2440 m near 17.3 E, 34.7 S, run backward in
+    time with 5-minute RK4 steps: they rise at 200 m/day to their 50 m
+    dwelling depth (vertical advection on the way), then live there for a
+    30-day lifespan during which their age counts, and sample temperature
+    along the way; deleted at the end of the lifespan.  Field constants carry
+    the sinking speed, the dwelling depth and the maximum age."""
+    gf = synth.GlobalField(res_deg=1.0, nz=30, nt=10, seed=5, kmax=40, period=10 * DAY)
+    spec = gf.spec(materialise=True)
+    temp = synth.temperature(spec.lon, spec.lat, spec.depth, spec.times, seed=4,
+                             period=spec.period).astype(np.float32)
+    rng = np.random.default_rng(7)
+    n = 800
+    lon = (17.3 + rng.uniform(-3, 3, n)).astype(np.float32)
+    lat = (-34.7 + rng.uniform(-3, 3, n)).astype(np.float32)
+    dep = np.full(n, 2440.0, np.float32)
+    t0, dt, T = 45 * DAY, -300.0, 45 * DAY
+    w_sink, dwell, max_age = 200.0 / DAY, 50.0, 30 * DAY
+    data = spec.data if pos == "f32" else spec.data.astype(np.float64)
+    o = _oracle(spec, data, (temp.astype(data.dtype),), O.LINEAR, (O.LINEAR,), lon, lat, dep, t0,
+                dt, T, ("settle", "age", "sample"), w_sink=w_sink, dwell=dwell,
+                max_age=max_age)
+    fs = pg.FieldSet.from_spec(spec, storage="f64" if pos == "f64" else "f32")
+    fs.add_scalar("temperature")
+    for s in range(spec.nt):
+        fs.load_scalar(0, s, temp[s])
+    fs.add_constant("w_sink", w_sink)
+    fs.add_constant("dwelling_depth", dwell)
+    fs.add_constant("max_age", max_age)
+    assert fs.get_constant("dwelling_depth") == dwell
+    ps = pg.ParticleSet(fs, lon, lat, dep, t0=t0, pos=pos)
+    k = pg.Kernel("rk4", ("settle", "age", "sample"), w_sink=None)
+    steps = ps.execute(k, T, dt, DAY)
+    # per particle at most one step apart (checked below): FP32 depths may
+    # reach the dwelling depth a step later or earlier
+    assert abs(steps - o["steps"]) <= (0 if pos == "f64" else n), (steps, o["steps"])
+    g, v = ps.get(), ps.get_variables()
+    np.testing.assert_array_equal(g["status"], o["status"])
+    done = o["status"] == 4
+    assert done.sum() > 0.9 * n
+    np.testing.assert_array_equal(g["depth"][done], np.full(done.sum(), dwell))
+    # the step that reaches the dwelling depth: where the two depths straddle
+    # 50 m at the end of a step, one side settles a step later (FP32 depth
+    # rounding); everywhere else steps, times and ages are equal
+    same = g["step"] == o["step"]
+    assert np.mean(same) > (0.999 if pos == "f64" else 0.95), np.mean(same)
+    assert np.all(np.abs(g["step"].astype(np.int64) - o["step"]) <= 1)
+    np.testing.assert_array_equal(g["time"][same], o["time"][same])
+    np.testing.assert_array_equal(v["age"][same], o["age"][same])
+    np.testing.assert_array_equal(v["age"][done], np.full(done.sum(), max_age))
+    done = done & same
+    e = cell_error(g, o, spec)[done]
+    if pos == "f64":
+        # spherical mesh: the platforms' cos may differ in the last ulp
+        assert np.max(e) < 1e-6, np.max(e)
+        np.testing.assert_allclose(v["vars"][0][done], o["vars"][0][done], rtol=0, atol=1e-9)
+    else:
+        assert np.mean(e) < 1e-3 and np.max(e) < 2e-2, (np.mean(e), np.max(e))
+        # the sampled temperature follows the position: its difference stays
+        # below the local change of the field over that distance (a bound of
+        # 2 degC per cell, with margin)
+        dT = np.abs(v["vars"][0][done] - o["vars"][0][done])
+        assert np.max(dT - 2.0 * e) < 1e-4, np.max(dT - 2.0 * e)
+
+
+def test_constants_and_variables_survive_checkpoint(pg, tmp_path):
+    rng = np.random.default_rng(47)
+    spec = _flat3d(rng, nt=4)
+    temp = synth.temperature(spec.lon, spec.lat, spec.depth, spec.times, seed=6)
+    n = 1500
+    lon = rng.uniform(spec.lon[1], spec.lon[-2], n)
+    lat = rng.uniform(spec.lat[1], spec.lat[-2], n)
+    dep = rng.uniform(spec.depth[1], spec.depth[-2], n)
+    fs = pg.FieldSet.from_spec(spec, storage="f64")
+    fs.add_scalar("T")
+    for s in range(spec.nt):
+        fs.load_scalar(0, s, temp[s])
+    fs.add_constant("Kh", 5.0)
+    fs.add_constant("max_age", 1.2 * DAY)
+    K = pg.Kernel("rk4", ("brownian", "age", "sample"), kh=None)
+    a = pg.ParticleSet(fs, lon, lat, dep, pos="f64", seed=9)
+    a.execute(K, 2 * DAY, 900.0)
+    ref, rv = a.get(), a.get_variables()
+    # the same with the constant given to the kernel directly
+    b = pg.ParticleSet(fs, lon, lat, dep, pos="f64", seed=9)
+    b.execute(pg.Kernel("rk4", ("brownian", "age", "sample"), kh=5.0), 2 * DAY, 900.0)
+    for k in ("lon", "lat", "status"):
+        np.testing.assert_array_equal(b.get()[k], ref[k])
+    # half, checkpoint, restore, other half
+    c = pg.ParticleSet(fs, lon, lat, dep, pos="f64", seed=9)
+    c.set_tune(resort_steps=13)
+    c.execute(K, DAY, 900.0)
+    c.save(tmp_path / "v.bin")
+    d = pg.ParticleSet.restore(fs, tmp_path / "v.bin")
+    d.execute(K, DAY, 900.0)
+    got, gv = d.get(), d.get_variables()
+    for k in ("lon", "lat", "depth", "time", "step", "status", "id"):
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
+    np.testing.assert_array_equal(gv["age"], rv["age"])
+    np.testing.assert_array_equal(gv["vars"], rv["vars"])
+    assert np.isnan(pg.ParticleSet(fs, lon[:5], lat[:5], dep[:5], pos="f64").get_variables()
+                    ["vars"]).all()
+
+
+def test_example_error_conventions(pg):
+    rng = np.random.default_rng(53)
+    spec = _flat3d(rng, nt=2)
+    fs = pg.FieldSet.from_spec(spec, storage="f32")
+    lon, lat, dep = spec.lon[[3]], spec.lat[[3]], spec.depth[[3]]
+    ps = pg.ParticleSet(fs, lon, lat, dep, pos="f32")
+    with pytest.raises(pg.PGError) as e:          # constant missing
+        ps.execute(pg.Kernel("rk4", ("age",)), 3600.0, 600.0)
+    assert e.value.code == -3
+    with pytest.raises(pg.PGError) as e:          # no scalar field to sample
+        ps.execute(pg.Kernel("rk4", ("sample",)), 3600.0, 600.0)
+    assert e.value.code == -3
+    with pytest.raises(pg.PGError) as e:
+        fs.get_constant("nothing")
+    assert e.value.code == -1
+    with pytest.raises(pg.PGError) as e:
+        fs.add_constant("bad", float("inf"))
+    assert e.value.code == -1
+    fs.add_constant("max_age", 100.0)
+    gs = synth.GlobalField(res_deg=10.0, nz=1, nt=2, seed=1, kmax=5, period=2 * DAY)
+    gspec = gs.spec(materialise=True)
+    fq = pg.FieldSet.from_spec(gspec, storage="f16")
+    fq.add_constant("max_age", 100.0)
+    pq = pg.ParticleSet(fq, np.array([10.0]), np.array([5.0]), pos="f32")
+    with pytest.raises(pg.PGError) as e:          # extended kernel needs FP32 storage
+        pq.execute(pg.Kernel("rk4", ("age",)), 3600.0, 600.0)
+    assert e.value.code == -8
+    fc = pg.FieldSet.from_spec(gspec, storage="f32")
+    fc.add_constant("max_age", 100.0)
+    pc = pg.ParticleSet(fc, np.array([10.0]), np.array([5.0]), pos="cell")
+    with pytest.raises(pg.PGError) as e:          # not in the cell form
+        pc.execute(pg.Kernel("rk4", ("age",)), 3600.0, 600.0)
+    assert e.value.code == -8
+    pb = pg.ParticleSet(fc, np.array([10.0]), np.array([5.0]), pos="f32")
+    with pytest.raises(pg.PGError) as e:          # not in the batched form
+        pg.execute_batch([pb], [pg.Kernel("rk4", ("age",))], [DAY], [600.0], tune=(64, 0))
+    assert e.value.code == -8

@@ -116,8 +116,10 @@ def test_backward_in_time_fp32_and_cell(pg, form, chunk):
     _outputs(g, o, spec, f"{form} chunk {chunk}")
 
 
-def test_backward_streamed_equals_resident(pg):
-    """Backward in time with snapshots streamed through the four-slot ring
+@pytest.mark.parametrize("ring", [4, 7])
+def test_backward_streamed_equals_resident(pg, ring):
+    """Backward in time with snapshots streamed through the ring (four slots:
+    one-day launches; seven: launches spanning up to four snapshot times)
     equals the resident field bit for bit."""
     spec = _global(nz=8, nt=5)
     lon, lat, dep = synth.uniform_particles(2000, 19, (0, 360), (-70, 70), (6.0, 900.0),
@@ -130,8 +132,11 @@ def test_backward_streamed_equals_resident(pg):
             fs = pg.FieldSet(spec.lon, spec.lat, spec.depth, mesh="spherical", periodic_lon=True,
                              nfields=spec.data.shape[1], storage="f32")
             fs.set_times(spec.times, spec.period)
+            fs.set_ring(ring)
             fs.stream([spec.data[s] for s in range(spec.nt)])
+            assert fs.device_bytes() == ring * 4 * 4 * np.prod(spec.data.shape[2:])
         ps = pg.ParticleSet(fs, lon, lat, dep, t0=4.75 * DAY, pos="f32")
-        res.append(gpu_run(ps, pg.Kernel("rk4"), 4.5 * DAY, -1800.0, DAY))
+        ps.set_tune(block=128, resort_steps=0, chunk_steps=400)
+        res.append(gpu_run(ps, pg.Kernel("rk4"), 4.5 * DAY, -1800.0, 2.25 * DAY))
     for k in ("lon", "lat", "depth", "status", "time", "step"):
         np.testing.assert_array_equal(res[1]["final"][k], res[0]["final"][k], err_msg=k)

@@ -307,19 +307,24 @@ def test_streamed_equals_resident(pg):
                                             dtype=np.float32)
     T = 4.5 * DAY
     res = []
-    for mode in ("resident", "ptrs", "callback"):
+    for mode in ("resident", "ptrs", "callback", "ring6"):
         if mode == "resident":
             fs = pg.FieldSet.from_spec(spec, storage="f32")
         else:
             fs = pg.FieldSet(spec.lon, spec.lat, spec.depth, mesh="spherical", periodic_lon=True,
                              nfields=spec.data.shape[1], storage="f32")
             fs.set_times(spec.times, spec.period)
-            if mode == "ptrs":
+            if mode == "ring6":
+                fs.set_ring(6)
+                fs.stream([spec.data[s] for s in range(spec.nt)])
+            elif mode == "ptrs":
                 fs.stream([spec.data[s] for s in range(spec.nt)])
             else:
                 fs.stream(callback=lambda s, out: out.__setitem__(Ellipsis, spec.data[s]))
         ps = pg.ParticleSet(fs, lon, lat, dep, pos="f32")
-        res.append(gpu_run(ps, pg.Kernel("rk4"), T, 1800.0, DAY))
+        if mode == "ring6":       # launches of up to three days across snapshot times
+            ps.set_tune(block=128, resort_steps=0, chunk_steps=200)
+        res.append(gpu_run(ps, pg.Kernel("rk4"), T, 1800.0, 2.25 * DAY if mode == "ring6" else DAY))
     for r in res[1:]:
         for k in ("lon", "lat", "depth", "status", "time"):
             np.testing.assert_array_equal(r["final"][k], res[0]["final"][k])
