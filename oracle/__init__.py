@@ -5,6 +5,7 @@ may import this package.  The CUDA library never does.
 """
 from .oracle import (  # noqa: F401
     ALIVE, OOB_HORIZ, OOB_DEPTH, NAN, DELETED, BROWNIAN, SINK, SETTLE, AGE, SAMPLE, EULER, RK4,
+    RKF45, rkf45_trial,
     LINEAR, NEAREST, build, lib, Field, Kernel, run, sample, sample_tracer, velocity, locate,
     locate_lon,
     wrap_lon, philox4x32_10, normal_pair, quantise, dequantise,

@@ -20,7 +20,7 @@ _OUT = os.path.join(_HERE, "_build", "libparcels_oracle.so")
 ALIVE, OOB_HORIZ, OOB_DEPTH, NAN, DELETED = 0, 1, 2, 3, 4
 BROWNIAN, SINK, SETTLE, AGE, SAMPLE = 1, 2, 4, 8, 16
 LINEAR, NEAREST = 0, 1
-EULER, RK4 = 0, 1
+EULER, RK4, RKF45 = 0, 1, 2
 FLAT, SPHERICAL = 0, 1
 DEG_M = 1852.0 * 60.0
 
@@ -56,7 +56,8 @@ class _Kernel(C.Structure):
     _fields_ = [
         ("scheme", C.c_int), ("behaviours", C.c_uint), ("kh", C.c_double),
         ("w_sink", C.c_double), ("seed", C.c_uint64), ("dwell_depth", C.c_double),
-        ("max_age", C.c_double),
+        ("max_age", C.c_double), ("rk45_tol", C.c_double), ("rk45_hmin", C.c_double),
+        ("rk45_hmax", C.c_double),
     ]
 
 
@@ -83,7 +84,10 @@ def lib():
             L.or_normal_pair.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, dp, dp]
             L.or_normal_pair.restype = None
             L.or_run.argtypes = [C.POINTER(_FieldSet), C.POINTER(_Kernel), C.c_int64] + \
-                [C.c_void_p] * 9 + [C.c_double, C.c_double, C.c_double, C.c_int]
+                [C.c_void_p] * 10 + [C.c_double, C.c_double, C.c_double, C.c_int]
+            L.or_rkf45_trial.argtypes = [C.POINTER(_FieldSet), C.c_double, C.c_double,
+                                         C.c_double, C.c_double, C.c_double, dp, dp]
+            L.or_rkf45_trial.restype = C.c_int
             L.or_sample_tracer.argtypes = [C.POINTER(_FieldSet), C.c_int, C.c_double,
                                            C.c_double, C.c_double, C.c_double, dp]
             L.or_sample_tracer.restype = C.c_int
@@ -138,19 +142,21 @@ class Field:
 
 class Kernel:
     def __init__(self, scheme=RK4, behaviours=0, kh=0.0, w_sink=0.0, seed=0, dwell_depth=0.0,
-                 max_age=0.0):
+                 max_age=0.0, rk45_tol=0.0, rk45_hmin=1.0, rk45_hmax=86400.0):
         self.k = _Kernel(int(scheme), int(behaviours), float(kh), float(w_sink), int(seed),
-                         float(dwell_depth), float(max_age))
+                         float(dwell_depth), float(max_age), float(rk45_tol), float(rk45_hmin),
+                         float(rk45_hmax))
 
 
 def run(field: Field, kernel: Kernel, lon, lat, depth, time, ids, step, status, dt,
-        t_stop, t_end=None, nthreads=None, age=None, variables=None):
+        t_stop, t_end=None, nthreads=None, age=None, variables=None, hstep=None):
     """Advance particles in place (arrays: float64 x4, uint64, uint32, uint8).
 
     Every live particle steps while its time is before ``t_stop`` and before
     ``t_end`` (in the direction of dt); the last step is shortened to land on
     ``t_end``.  ``age`` (float64 [n]) and ``variables`` (float64 [ntracers, n])
-    are updated by the AGE and SAMPLE behaviours.  Returns the number of
+    are updated by the AGE and SAMPLE behaviours; ``hstep`` (float64 [n]) holds
+    the RKF45 step lengths (0: start from dt).  Returns the number of
     particle-steps taken.
     """
     if t_end is None:
@@ -161,19 +167,29 @@ def run(field: Field, kernel: Kernel, lon, lat, depth, time, ids, step, status, 
                    (time, np.float64), (ids, np.uint64), (step, np.uint32), (status, np.uint8)):
         assert a.dtype == dt_ and a.flags.c_contiguous
     n = len(lon)
-    for a, shape in ((age, (n,)), (variables, (len(field.tracers), n))):
+    for a, shape in ((age, (n,)), (variables, (len(field.tracers), n)), (hstep, (n,))):
         if a is not None:
             assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == shape
     r = lib().or_run(C.byref(field.s), C.byref(kernel.k), n, _ptr(lon), _ptr(lat), _ptr(depth),
                      _ptr(time), _ptr(ids), _ptr(step), _ptr(status),
                      _ptr(age) if age is not None else None,
-                     _ptr(variables) if variables is not None else None, float(dt),
+                     _ptr(variables) if variables is not None else None,
+                     _ptr(hstep) if hstep is not None else None, float(dt),
                      float(t_stop), float(t_end), int(nthreads))
     if r == -2:
         raise ValueError("the SAMPLE behaviour needs the variables array")
     if r < 0:
         raise ValueError("time span outside the field's time range")
     return int(r)
+
+
+def rkf45_trial(field: Field, t, lon, lat, depth, h):
+    """One RKF45 trial: (status, fourth-order position, error in metres)."""
+    out = (C.c_double * 3)()
+    err = C.c_double()
+    r = lib().or_rkf45_trial(C.byref(field.s), float(lon), float(lat), float(depth), float(t),
+                             float(h), out, C.byref(err))
+    return r, np.array(out[:]), err.value
 
 
 def sample_tracer(field: Field, tr, t, lon, lat, depth=0.0):

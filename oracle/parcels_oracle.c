@@ -42,7 +42,19 @@
  *         the dwelling depth); once age >= max_age the particle is deleted with
  *         status 4 and keeps the step's result;
  *       sample: each scalar field is interpolated at the step's new position
- *         and time into the particle's variable (NaN where the field is NaN).
+ *         and time into the particle's variable (NaN where the field is NaN);
+ *   - adaptive RKF45 (Sect. 2.1.1 names Runge-Kutta-Fehlberg): the Fehlberg
+ *     4(5) pair; a trial step of length h gives the fourth-order X4 and the
+ *     fifth-order X5; its error is the largest of |X5 - X4| over the axes in
+ *     metres (degrees times metres per degree on a sphere, at the latitude of
+ *     X4); the trial is accepted when the error is at most the tolerance or
+ *     |h| is at the minimum step, and the particle moves to X4; a rejected
+ *     trial halves the particle's step length (not below the minimum) and is
+ *     repeated from the same state; after an accepted step whose error is
+ *     below a tenth of the tolerance, taken at the particle's full step
+ *     length, that length doubles (not above the maximum).  Each particle
+ *     keeps its step length between steps and executes; a step is shortened
+ *     to land on the stop time (the next output time) and on the end time.
  * Philox4x32-10 is pinned by the generator's published known-answer vectors;
  * the word-to-uniform mapping of Box-Muller by a value computed by hand from
  * one of them.
@@ -84,6 +96,8 @@ typedef struct {
     uint64_t seed;
     double dwell_depth;           /* settle: depth where the vertical move ends */
     double max_age;               /* age: deletion age in seconds              */
+    double rk45_tol;              /* RKF45: error tolerance per step, metres   */
+    double rk45_hmin, rk45_hmax;  /* RKF45: smallest and largest step, seconds */
 } or_kernel;
 
 enum { OR_ALIVE = 0, OR_OOB_HORIZ = 1, OR_OOB_DEPTH = 2, OR_NAN = 3, OR_DELETED = 4 };
@@ -387,6 +401,63 @@ static int out_of_domain(const or_fieldset *fs, double lon, double lat, double d
  * 0 returned (OR_DELETED when the age behaviour deleted it, with the new state
  * written); otherwise the state is left untouched and the status returned.
  * age and vars (stride vstride between variables) are written on success. */
+static int finish_step(const or_fieldset *fs, const or_kernel *kn, double *plon, double *plat,
+                       double *pdep, double t, double h, uint64_t id, uint32_t step,
+                       double *page, double *pvars, int64_t vstride,
+                       double nlon, double nlat, double ndep);
+
+/* The Fehlberg 4(5) pair: stage times c, stage weights a (row i uses stages
+ * 0..i-1), fourth- and fifth-order weights b4, b5. */
+static const double RKF_C[6] = {0.0, 1.0 / 4.0, 3.0 / 8.0, 12.0 / 13.0, 1.0, 1.0 / 2.0};
+static const double RKF_A[6][5] = {
+    {0, 0, 0, 0, 0},
+    {1.0 / 4.0, 0, 0, 0, 0},
+    {3.0 / 32.0, 9.0 / 32.0, 0, 0, 0},
+    {1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0, 0, 0},
+    {439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0, 0},
+    {-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0}};
+static const double RKF_B4[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0};
+static const double RKF_B5[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0,
+                                 -9.0 / 50.0, 2.0 / 55.0};
+
+/* One RKF45 trial of length h from (lon, lat, dep) at t: the fourth-order
+ * position in out4 and the error estimate in metres.  Returns 0 or the
+ * status of a stage (out of the domain, NaN velocity). */
+int or_rkf45_trial(const or_fieldset *fs, double lon, double lat, double dep, double t,
+                   double h, double *out4, double *err_m)
+{
+    double k[6][3];
+    for (int i = 0; i < 6; ++i) {
+        double px = lon, py = lat, pz = dep;
+        for (int j = 0; j < i; ++j) {
+            px = px + h * RKF_A[i][j] * k[j][0];
+            py = py + h * RKF_A[i][j] * k[j][1];
+            pz = pz + h * RKF_A[i][j] * k[j][2];
+        }
+        int r = or_velocity(fs, t + RKF_C[i] * h, px, py, pz, k[i]);
+        if (r) return r;
+    }
+    double d4[3] = {0, 0, 0}, d5[3] = {0, 0, 0};
+    for (int i = 0; i < 6; ++i)
+        for (int q = 0; q < 3; ++q) {
+            d4[q] = d4[q] + RKF_B4[i] * k[i][q];
+            d5[q] = d5[q] + RKF_B5[i] * k[i][q];
+        }
+    out4[0] = lon + h * d4[0];
+    out4[1] = lat + h * d4[1];
+    out4[2] = dep + h * d4[2];
+    double ex = fabs(h * (d5[0] - d4[0])), ey = fabs(h * (d5[1] - d4[1]));
+    double ez = fabs(h * (d5[2] - d4[2]));
+    if (fs->mesh == 1) {
+        const double deg2rad = 3.14159265358979323846 / 180.0;
+        ex = ex * fs->deg_m * cos(out4[1] * deg2rad);
+        ey = ey * fs->deg_m;
+    }
+    double e = ex > ey ? ex : ey;
+    *err_m = e > ez ? e : ez;
+    return 0;
+}
+
 static int step_one(const or_fieldset *fs, const or_kernel *kn, double *plon, double *plat,
                     double *pdep, double t, double h, uint64_t id, uint32_t step,
                     double *page, double *pvars, int64_t vstride)
@@ -413,6 +484,19 @@ static int step_one(const or_fieldset *fs, const or_kernel *kn, double *plon, do
         nlat = lat + (k1[1] + 2.0 * k2[1] + 2.0 * k3[1] + k4[1]) / 6.0 * h;
         ndep = dep + (k1[2] + 2.0 * k2[2] + 2.0 * k3[2] + k4[2]) / 6.0 * h;
     }
+    return finish_step(fs, kn, plon, plat, pdep, t, h, id, step, page, pvars, vstride,
+                       nlon, nlat, ndep);
+}
+
+/* The part of a step after advection: behaviours, the zonal wrap, the
+ * domain test, and on success the new state, age and sampled variables. */
+static int finish_step(const or_fieldset *fs, const or_kernel *kn, double *plon, double *plat,
+                       double *pdep, double t, double h, uint64_t id, uint32_t step,
+                       double *page, double *pvars, int64_t vstride,
+                       double nlon, double nlat, double ndep)
+{
+    double dep = *pdep;
+    int r;
     if (kn->behaviours & OR_BROWNIAN) {
         double n1, n2;
         or_normal_pair(kn->seed, id, step, &n1, &n2);
@@ -468,11 +552,56 @@ typedef struct {
     uint32_t *step;
     uint8_t *status;
     double *age, *vars;            /* age[n], vars[ntracers][n]; may be NULL */
+    double *hstep;                 /* RKF45 step lengths [n]; may be NULL      */
     int64_t n;
     double dt, t_stop, t_end;
     int64_t begin, end;
     int64_t steps_done;
 } or_job;
+
+/* RKF45 steps of particle p from time *pt while its time lies before t_stop
+ * and t_end; returns the steps taken. */
+static int64_t run_rkf45(or_job *jb, int64_t p, double *pt)
+{
+    const or_kernel *kn = jb->kn;
+    double sgn = jb->dt > 0.0 ? 1.0 : -1.0;
+    double t = *pt;
+    double hp = jb->hstep ? jb->hstep[p] : 0.0;
+    if (!(sgn * hp > 0.0)) hp = jb->dt;
+    int64_t done = 0;
+    double target = sgn * (jb->t_stop - jb->t_end) < 0.0 ? jb->t_stop : jb->t_end;
+    while (sgn * (jb->t_stop - t) > 0.0 && sgn * (jb->t_end - t) > 0.0) {
+        double h = hp;
+        int clipped = 0;
+        if (sgn * (target - t) < sgn * h) { h = target - t; clipped = 1; }
+        double x4[3], err;
+        int r = or_rkf45_trial(jb->fs, jb->lon[p], jb->lat[p], jb->depth[p], t, h, x4, &err);
+        if (r) { jb->status[p] = (uint8_t)r; break; }
+        if (err > kn->rk45_tol && fabs(h) > kn->rk45_hmin) {
+            double nh = fabs(h) / 2.0;
+            if (nh < kn->rk45_hmin) nh = kn->rk45_hmin;
+            hp = sgn * nh;
+            continue;
+        }
+        double age_dummy = 0.0;
+        r = finish_step(jb->fs, kn, &jb->lon[p], &jb->lat[p], &jb->depth[p], t, h, jb->id[p],
+                        jb->step[p], jb->age ? &jb->age[p] : &age_dummy,
+                        jb->vars ? &jb->vars[p] : NULL, jb->n, x4[0], x4[1], x4[2]);
+        if (r && r != OR_DELETED) { jb->status[p] = (uint8_t)r; break; }
+        t = t + h;
+        jb->step[p] += 1u;
+        ++done;
+        if (!clipped && err < kn->rk45_tol / 10.0) {
+            double nh = 2.0 * fabs(hp);
+            if (nh > kn->rk45_hmax) nh = kn->rk45_hmax;
+            hp = sgn * nh;
+        }
+        if (r == OR_DELETED) { jb->status[p] = (uint8_t)r; break; }
+    }
+    if (jb->hstep) jb->hstep[p] = hp;
+    *pt = t;
+    return done;
+}
 
 /* A particle steps while its time lies before t_stop and before t_end (in the
  * direction of dt); the step length is dt, shortened only to land on t_end. */
@@ -484,6 +613,11 @@ static void *run_range(void *arg)
     for (int64_t p = jb->begin; p < jb->end; ++p) {
         if (jb->status[p] != OR_ALIVE) continue;
         double t = jb->time[p];
+        if (jb->kn->scheme == 2) {
+            done += run_rkf45(jb, p, &t);
+            jb->time[p] = t;
+            continue;
+        }
         while (sgn * (jb->t_stop - t) > 0.0 && sgn * (jb->t_end - t) > 0.0) {
             double h = jb->dt;
             if (sgn * (jb->t_end - t) < sgn * h) h = jb->t_end - t;
@@ -513,8 +647,8 @@ static void *run_range(void *arg)
  * the time span leaves a non-periodic field's time range. */
 int64_t or_run(const or_fieldset *fs, const or_kernel *kn, int64_t n, double *lon,
                double *lat, double *depth, double *time, const uint64_t *id,
-               uint32_t *step, uint8_t *status, double *age, double *vars, double dt,
-               double t_stop, double t_end, int nthreads)
+               uint32_t *step, uint8_t *status, double *age, double *vars, double *hstep,
+               double dt, double t_stop, double t_end, int nthreads)
 {
     if (n <= 0) return 0;
     if ((kn->behaviours & OR_SAMPLE) && fs->ntracers > 0 && !vars) return -2;
@@ -535,7 +669,7 @@ int64_t or_run(const or_fieldset *fs, const or_kernel *kn, int64_t n, double *lo
         jb->fs = fs; jb->kn = kn;
         jb->lon = lon; jb->lat = lat; jb->depth = depth; jb->time = time;
         jb->id = id; jb->step = step; jb->status = status;
-        jb->age = age; jb->vars = vars; jb->n = n;
+        jb->age = age; jb->vars = vars; jb->hstep = hstep; jb->n = n;
         jb->dt = dt; jb->t_stop = t_stop; jb->t_end = t_end;
         jb->begin = (int64_t)w * chunk;
         jb->end = jb->begin + chunk < n ? jb->begin + chunk : n;
