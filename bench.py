@@ -54,10 +54,15 @@ def parse():
                     help="snapshot ring slots of the end-to-end leg (4: two in use + the next)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="3d", choices=["3d", "precision", "batch", "surrogate"],
+    ap.add_argument("--workload", default="3d",
+                    choices=["3d", "precision", "batch", "surrogate", "example", "rkf45"],
                     help="3d: the FP32 3-D workload (default); precision: 2-D 1/12 deg "
                          "cell-index + FP16/BF16 form against plain FP32; batch: 256 "
-                         "releases in one persistent launch per day, graph-captured")
+                         "releases in one persistent launch per day, graph-captured; "
+                         "example: the worked example's backward two-phase run with "
+                         "sampled temperature and daily indexed output; rkf45: adaptive "
+                         "RKF45 on the 3-D workload")
+    ap.add_argument("--rkf45-tol", type=float, default=10.0, help="metres per step")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="shrink every release of the batch workload (tests)")
     ap.add_argument("--train-segments", type=int, default=20_000_000)
@@ -240,6 +245,8 @@ def main():
         return batch_workload(args, rank, world, local)
     if args.workload == "surrogate":
         return surrogate_workload(args, rank, world, local)
+    if args.workload in ("example", "rkf45"):
+        return example_or_rkf45_workload(args, rank, world, local)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -317,9 +324,13 @@ def main():
     e2e, streamed = None, None
     if not args.no_e2e and host_field is not None:
         streamed = {f"ring{r}": streamed_leg(pg, gf, torch, host_field, lon, lat, dep, kern,
-                                             runtime, args, r, False) for r in (4, 10)}
+                                             runtime, args, r, False) for r in (4,)}
         e2e = streamed_leg(pg, gf, torch, host_field, lon, lat, dep, kern, runtime, args,
                            args.e2e_ring, True)
+
+    output = None
+    if not args.no_e2e:
+        output = output_leg(pg, fs, torch, dlon, dlat, ddep, kern, runtime, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and host_field is not None:
@@ -385,6 +396,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "streamed": streamed,
+        "output": output,
         "gpu_launches": int(c1.value - c0.value),
         "clocks": clk,
         "particle_steps": total_all,
@@ -393,6 +405,53 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def output_leg(pg, fs, torch, dlon, dlat, ddep, kern, runtime, args):
+    """Trajectory output at scale (the ParticleFile of Sect. 3): the same
+    resident run with daily output in the indexed form through the pinned
+    ring (rows packed on the GPU, copied on a side stream, handed to a hook
+    that only counts them), against the run without output.  Best of two,
+    device-timed around the execute."""
+    import ctypes as C
+    lib = pg.load()
+    rows = [0, 0]
+
+    def hook(user, rp):
+        rows[0] += rp.contents.n
+        rows[1] += 1
+        return 0
+    cb = pg._native.RECORD_CB(hook)
+    res = {}
+    for mode in ("none", "indexed_daily"):
+        best = None
+        for _ in range(2):
+            ps = pg.ParticleSet(fs, dlon, dlat, ddep, pos="f32", seed=0)
+            ps.set_tune(args.block, args.resort_steps, args.chunk_steps)
+            rows[0] = rows[1] = 0
+            steps = C.c_int64()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record()
+            if mode == "none":
+                r = lib.pg_execute(ps.h, kern.h, runtime, 1800.0, 0.0, pg._native.OUTPUT_CB(),
+                                   None, None, C.byref(steps))
+            else:
+                r = lib.pg_execute_records(ps.h, kern.h, runtime, 1800.0, DAY, 1, cb, None, None,
+                                           C.byref(steps))
+            ev1.record()
+            torch.cuda.synchronize()
+            assert r == 0, lib.pg_last_error()
+            ms = ev0.elapsed_time(ev1)
+            ps.destroy()
+            if best is None or ms < best[0]:
+                best = (ms, steps.value, rows[0], rows[1])
+        res[mode] = {"ms": best[0], "particle_steps_per_s": best[1] / (best[0] / 1e3),
+                     "rows": best[2], "outputs": best[3]}
+    n = len(dlon)
+    res["ring_bytes_per_output"] = n * (8 * 5 + 1)
+    res["overhead"] = res["indexed_daily"]["ms"] / res["none"]["ms"] - 1.0
+    return res
 
 
 def streamed_leg(pg, gf, torch, host_field, lon, lat, dep, kern, runtime, args, ring,
@@ -497,6 +556,131 @@ def reference_arm(args, rank, world):
         "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def example_or_rkf45_workload(args, rank, world, local):
+    """example: the paper's worked example (Sect. 3) at scale on the 3-D
+    1/4-degree field with a synthetic temperature field: particles released
+    around 17.3 E, 34.7 S at 2440 m are run backward in time with 5-minute
+    RK4 steps; they rise at 200 m/day to their 50 m dwelling depth, live
+    there 30 days (age), sample temperature every step, and go to a daily
+    indexed trajectory output through the pinned ring.  rkf45: the 3-D
+    workload's particles and horizon with adaptive RKF45 steps (tolerance
+    --rkf45-tol metres, steps between 60 s and 2 h).  Each is compared with
+    plain FP32 RK4 at dt 30 min on the same particles."""
+    import ctypes as C
+    import torch
+    import paper_1707_05163_gb300 as pg
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gf = synth.GlobalField(res_deg=0.25, nz=50, nt=30, seed=2, period=30 * DAY)
+    fs = build_fieldset_device(pg, gf, torch, dev, make_field_host_bases(gf))
+    lib = pg.load()
+    example = args.workload == "example"
+    if example:
+        n = args.particles if args.particles != 10_000_000 else 1_000_000
+        rng = np.random.default_rng(11)
+        lon = (17.3 + rng.uniform(-2.0, 2.0, n)).astype(np.float32)
+        lat = (-34.7 + rng.uniform(-2.0, 2.0, n)).astype(np.float32)
+        dep = np.full(n, 2440.0, np.float32)
+        fs.add_scalar("temperature")
+        base = synth.temperature_base(gf.lon, gf.lat, gf.depth, seed=4, dtype=np.float32)
+        for s in range(len(gf.times)):
+            fs.load_scalar(0, s, torch.from_numpy(synth.temperature_at(base, gf.times[s],
+                                                                       gf.period)).to(dev))
+        del base
+        fs.add_constant("w_sink", 200.0 / DAY)
+        fs.add_constant("dwelling_depth", 50.0)
+        fs.add_constant("max_age", 30 * DAY)
+        kern = pg.Kernel("rk4", ("settle", "age", "sample"), w_sink=None)
+        t0, runtime, dt = 45 * DAY, 45 * DAY, -300.0
+    else:
+        n = args.particles
+        lon, lat, dep = synth.uniform_particles(n, 2, (0.0, 360.0), (-80.0, 80.0),
+                                                (5.0, 1000.0), dtype=np.float32)
+        fs.add_constant("rkf45_tol", args.rkf45_tol)
+        fs.add_constant("rkf45_min_dt", 60.0)
+        fs.add_constant("rkf45_max_dt", 7200.0)
+        kern = pg.Kernel("rkf45")
+        t0, runtime, dt = 0.0, args.days * DAY, 1800.0
+    dl, da, dd = (torch.from_numpy(a).to(dev) for a in (lon, lat, dep))
+    rows = [0, 0]
+
+    def hook(user, rp):
+        rows[0] += rp.contents.n
+        rows[1] += 1
+        return 0
+    cb = pg._native.RECORD_CB(hook)
+
+    def run(k, step_dt, timed):
+        ps = pg.ParticleSet(fs, dl, da, dd, t0=t0 if example else 0.0, pos="f32", seed=1)
+        ps.set_tune(args.block, args.resort_steps, args.chunk_steps)
+        lib.pg_pset_kernel_timing(ps.h, 1, None, None)
+        rows[0] = rows[1] = 0
+        steps = C.c_int64()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        if example and k is kern:
+            r = lib.pg_execute_records(ps.h, k.h, runtime, step_dt, DAY, 1, cb, None, None,
+                                       C.byref(steps))
+        else:
+            r = lib.pg_execute(ps.h, k.h, runtime, step_dt, 0.0, pg._native.OUTPUT_CB(), None,
+                               None, C.byref(steps))
+        ev1.record()
+        torch.cuda.synchronize()
+        assert r == 0, lib.pg_last_error()
+        kms, kl = C.c_double(), C.c_int64()
+        lib.pg_pset_kernel_timing(ps.h, -1, C.byref(kms), C.byref(kl))
+        g = ps.get() if timed else None
+        v = ps.get_variables() if (timed and example) else None
+        ps.destroy()
+        return steps.value, ev0.elapsed_time(ev1), kms.value, g, v
+
+    for _ in range(max(1, args.warmup)):
+        run(kern, dt, False)
+    clocks = ClockSampler(local)
+    best = None
+    for _ in range(max(1, args.steps)):
+        r = run(kern, dt, True)
+        if best is None or r[1] < best[1]:
+            best = r
+    clk = clocks.stop()
+    steps, ms, kms, g, v = best
+    plain = run(pg.Kernel("rk4"), -1800.0 if example else 1800.0, False)
+    line = {
+        "metric": METRIC, "value": steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded k^-3 random streamfunction field, synthetic temperature)",
+        "config": {"workload": ("worked example, backward: %d particles at 2440 m near 17.3E "
+                                "34.7S, RK4 dt 5 min, rise at 200 m/day to 50 m, 30-day "
+                                "lifespan, temperature sampled, daily indexed output, 3-D "
+                                "1/4 deg field" % n) if example else
+                               ("RKF45 on the 3-D workload: %d particles, %g days, tol %g m, "
+                                "steps 60 s to 2 h" % (n, args.days, args.rkf45_tol)),
+                   "block": args.block, "resort_steps": args.resort_steps,
+                   "chunk_steps": args.chunk_steps},
+        "particle_steps": steps, "advection_kernel_ms": kms,
+        "plain_fp32_rk4_30min": {"particle_steps": plain[0], "ms": plain[1],
+                                 "particle_steps_per_s": plain[0] / (plain[1] / 1e3)},
+        "clocks": clk,
+    }
+    if example:
+        st = g["status"]
+        line["example"] = {"output_rows": rows[0], "outputs": rows[1],
+                           "deleted_by_age": int((st == 4).sum()), "alive": int((st == 0).sum()),
+                           "out_of_domain": int(((st == 1) | (st == 2)).sum()),
+                           "mean_lifespan_temperature_at_death_degC":
+                               float(np.nanmean(v["vars"][0][st == 4])) if (st == 4).any() else None}
+    else:
+        alive = g["status"] == 0
+        line["rkf45"] = {"mean_steps_per_particle": float(g["step"][alive].mean()),
+                         "min_steps": int(g["step"][alive].min()),
+                         "max_steps": int(g["step"][alive].max()),
+                         "fixed_rk4_steps_per_particle": args.days * DAY / 1800.0}
+    print(json.dumps(line), flush=True)
 
 
 def surrogate_workload(args, rank, world, local):

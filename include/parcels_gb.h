@@ -81,9 +81,19 @@ typedef int pg_status;
 #define PG_POS_F32 1
 #define PG_POS_CELL 2
 
-/* Time-stepping scheme (Sect. 2.1.1). */
+/* Time-stepping scheme (Sect. 2.1.1).  PG_RKF45: adaptive Runge-Kutta-
+ * Fehlberg 4(5); each particle keeps its own step length (starting from the
+ * execute's |dt|, at most the field set constant "rkf45_max_dt" (default
+ * |dt|), at least "rkf45_min_dt" (default 1 s)); a trial whose error (the
+ * largest of |X5 - X4| over the axes, in metres) exceeds "rkf45_tol" (metres,
+ * required) is repeated at half the length; an accepted step with a tenth of
+ * the tolerance doubles the length; steps land on output times and the end
+ * time; the particle moves to the fourth-order X4.  Needs lon/lat/depth
+ * positions and FP32 or FP64 storage (PG_POS_F32 with PG_F32), outside
+ * pg_execute_batch. */
 #define PG_EULER 0
 #define PG_RK4 1
+#define PG_RKF45 2
 
 /* Behaviour bits, applied after advection in this order.  SETTLE, AGE and
  * SAMPLE are the custom kernels of the paper's worked example (Sect. 3; the

@@ -18,7 +18,7 @@ PG_ERR_CALLBACK, PG_ERR_TIMEOUT, PG_ERR_NOMEM, PG_ERR_UNSUPPORTED, PG_ERR_DEVICE
 PG_FLAT, PG_SPHERICAL = 0, 1
 PG_F64, PG_F32, PG_F16S, PG_BF16S = 0, 1, 2, 3
 PG_POS_F64, PG_POS_F32, PG_POS_CELL = 0, 1, 2
-PG_EULER, PG_RK4 = 0, 1
+PG_EULER, PG_RK4, PG_RKF45 = 0, 1, 2
 PG_BROWNIAN, PG_SINK, PG_SETTLE, PG_AGE, PG_SAMPLE = 1, 2, 4, 8, 16
 PG_LINEAR, PG_NEAREST = 0, 1
 PG_ALIVE, PG_OOB_HORIZ, PG_OOB_DEPTH, PG_NAN, PG_DELETED = 0, 1, 2, 3, 4

@@ -216,7 +216,8 @@ class Kernel:
         for b in self.behaviours:
             bits |= _BEH[b]
         h = C.c_void_p()
-        N.check(self._lib.pg_kernel_create({"euler": N.PG_EULER, "rk4": N.PG_RK4}[scheme], bits,
+        N.check(self._lib.pg_kernel_create({"euler": N.PG_EULER, "rk4": N.PG_RK4,
+                                            "rkf45": N.PG_RKF45}[scheme], bits,
                                            self.kh, self.w_sink, C.byref(h)))
         self.h = h
 

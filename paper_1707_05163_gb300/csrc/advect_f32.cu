@@ -27,7 +27,7 @@ static cudaError_t launch_f32(const StepArgs &a, int block, cudaStream_t st) {
 cudaError_t launch_advect_plain(const StepArgs &a, int real, int storage, int block,
                                 cudaStream_t st) {
   if (real == PG_POS_F64) return launch_advect_f64(a, storage, block, st);
-  if ((a.k.beh & (BEH_SETTLE | BEH_AGE | BEH_SAMPLE)) || a.f.nearest)
+  if ((a.k.beh & (BEH_SETTLE | BEH_AGE | BEH_SAMPLE)) || a.f.nearest || a.k.scheme == 2)
     return storage == PG_F32 ? launch_advect_plain_ext(a, block, st) : cudaErrorNotSupported;
   switch (storage) {
     case PG_F32: return launch_f32<float>(a, block, st);

@@ -204,6 +204,11 @@ __device__ __forceinline__ int velocity(const A &a, Sampler<Real, Store, NF, D3,
 __device__ __forceinline__ double dwell_of(const KernArgs &k, double) { return k.dwell; }
 __device__ __forceinline__ float dwell_of(const KernArgs &k, float) { return k.dwell_f; }
 
+template <bool EXT, typename Real, typename Store, int NF, bool D3, int GEO, class A>
+__device__ __forceinline__ int finish_step(const A &a, Real &lon, Real &lat, Real &dep, Real nlon,
+                                           Real nlat, Real ndep, Real hr, double h64,
+                                           double &age, const uint64_t *idp, uint32_t stp);
+
 // One step of Eq. 1.  Returns 0 and updates (lon, lat, dep) on success.
 // RK4 stages run in a loop: stage s samples at (X + k_{s-1} c_s h, t + c_s h)
 // with c = (0, 1/2, 1/2, 1) and accumulates ((k1 + 2 k2) + 2 k3) + k4.
@@ -274,6 +279,20 @@ __device__ __forceinline__ int step_one(const A &a, Sampler<Real, Store, NF, D3,
     nlat = lat + acc[1] / (Real)6 * hr;
     ndep = dep + acc[2] / (Real)6 * hr;
   }
+  return finish_step<EXT, Real, Store, NF, D3, GEO>(a, lon, lat, dep, nlon, nlat, ndep, hr, h64,
+                                                    age, idp, stp);
+}
+
+// The part of a step after advection, from the advected position (nlon,
+// nlat, ndep): behaviours (Brownian, sinking; settle), the zonal wrap, the
+// domain test; on success the new state and the age.  Returns 0, a status
+// (state untouched), or STATUS_DELETED (state updated).
+template <bool EXT, typename Real, typename Store, int NF, bool D3, int GEO, class A>
+__device__ __forceinline__ int finish_step(const A &a, Real &lon, Real &lat, Real &dep, Real nlon,
+                                           Real nlat, Real ndep, Real hr, double h64,
+                                           double &age, const uint64_t *idp, uint32_t stp) {
+  constexpr bool X = EXT || sizeof(Real) == 8;
+  int r;
   if (a.k.beh & 1u) {
     Real n1, n2;
     normal_pair(a.k.seed, *idp, stp, n1, n2);
@@ -319,6 +338,107 @@ __device__ __forceinline__ int step_one(const A &a, Sampler<Real, Store, NF, D3,
   return 0;
 }
 
+// ------------------------------------------------------------------ RKF45
+// The Fehlberg 4(5) pair (Sect. 2.1.1 names Runge-Kutta-Fehlberg): stage
+// times, stage weights, fourth- and fifth-order weights.
+__device__ constexpr double kRkfC[6] = {0.0, 1.0 / 4.0, 3.0 / 8.0, 12.0 / 13.0, 1.0, 1.0 / 2.0};
+__device__ constexpr double kRkfA[6][5] = {
+    {0, 0, 0, 0, 0},
+    {1.0 / 4.0, 0, 0, 0, 0},
+    {3.0 / 32.0, 9.0 / 32.0, 0, 0, 0},
+    {1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0, 0, 0},
+    {439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0, 0},
+    {-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0}};
+__device__ constexpr double kRkfB4[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0,
+                                         -1.0 / 5.0, 0.0};
+__device__ constexpr double kRkfB5[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0,
+                                         28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+
+// One trial of length h from (lon, lat, dep) at the clock's step start: the
+// fourth-order position x4 and the error estimate in metres (the largest
+// over the axes of |X5 - X4|, degrees turned into metres at the latitude of
+// X4 on a sphere).  Returns 0, a particle status, or -1 (internal failure).
+template <bool EXT, typename Real, typename Store, int NF, bool D3, int GEO, class A>
+__device__ __forceinline__ int rkf45_trial(const A &a, Sampler<Real, Store, NF, D3, GEO> &c,
+                                           Clock &ck, Real lon, Real lat, Real dep, Real h,
+                                           Real (&x4)[3], Real &err) {
+  Real k[6][3];
+  int r;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    Real px = lon, py = lat, pz = dep;
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      px = px + h * (Real)kRkfA[i][j] * k[j][0];
+      py = py + h * (Real)kRkfA[i][j] * k[j][1];
+      pz = pz + h * (Real)kRkfA[i][j] * k[j][2];
+    }
+    if ((r = velocity<EXT>(a, c, ck, (Real)kRkfC[i] * h, px, py, pz, k[i]))) return r;
+  }
+  Real d4[3] = {(Real)0, (Real)0, (Real)0}, d5[3] = {(Real)0, (Real)0, (Real)0};
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      d4[q] = d4[q] + (Real)kRkfB4[i] * k[i][q];
+      d5[q] = d5[q] + (Real)kRkfB5[i] * k[i][q];
+    }
+  x4[0] = lon + h * d4[0];
+  x4[1] = lat + h * d4[1];
+  x4[2] = dep + h * d4[2];
+  Real ex = pg_fabs(h * (d5[0] - d4[0])), ey = pg_fabs(h * (d5[1] - d4[1]));
+  const Real ez = pg_fabs(h * (d5[2] - d4[2]));
+  if (is_sph<GEO>(a.g)) {
+    ex = ex * (Real)a.k.deg_m * cos_deg(x4[1]);
+    ey = ey * (Real)a.k.deg_m;
+  }
+  const Real e = ex > ey ? ex : ey;
+  err = e > ez ? e : ez;
+  return 0;
+}
+
+// RKF45 steps of one particle while its time lies before t_stop and t_end:
+// trials rejected above the tolerance halve the particle's step length, an
+// accepted full-length step with a tenth of the tolerance doubles it, and
+// steps are shortened to land on t_clip (the next output time) and t_end.
+// Returns the steps taken; writes the state, status and step length back
+// through the references.
+template <bool EXT, typename Real, typename Store, int NF, bool D3, int GEO, class A>
+__device__ __forceinline__ unsigned long long rkf45_steps(
+    const A &a, Sampler<Real, Store, NF, D3, GEO> &c, Real &lon, Real &lat, Real &dep, double &t,
+    uint32_t &stp, double &hp, double &age, uint8_t &st, const uint64_t *idp) {
+  const double sgn = a.dt > 0.0 ? 1.0 : -1.0;
+  if (!(sgn * hp > 0.0)) hp = a.dt;
+  const double target = sgn * (a.t_clip - a.t_end) < 0.0 ? a.t_clip : a.t_end;
+  unsigned long long done = 0;
+  Clock ck;
+  ck.dt = 0.0; ck.k = 0;
+  while (sgn * (a.t_stop - t) > 0.0 && sgn * (a.t_end - t) > 0.0) {
+    double h = hp;
+    bool clipped = false;
+    if (sgn * (target - t) < sgn * h) { h = target - t; clipped = true; }
+    ck.t = t;
+    if constexpr (sizeof(Real) == 4) ck.d = c.s0 >= 0 ? (float)(t - c.ta) : 0.f;
+    Real x4[3], err;
+    int r = rkf45_trial<EXT>(a, c, ck, lon, lat, dep, (Real)h, x4, err);
+    if (r > 0) { st = (uint8_t)r; break; }
+    if (r < 0) break;
+    if ((double)err > a.k.rk_tol && fabs(h) > a.k.rk_hmin) {
+      hp = sgn * fmax(fabs(h) / 2.0, a.k.rk_hmin);
+      continue;
+    }
+    r = finish_step<EXT, Real, Store, NF, D3, GEO>(a, lon, lat, dep, x4[0], x4[1], x4[2],
+                                                  (Real)h, h, age, idp, stp);
+    if (r > 0 && r != STATUS_DELETED) { st = (uint8_t)r; break; }
+    t = t + h;
+    ++stp;
+    ++done;
+    if (!clipped && (double)err < a.k.rk_tol / 10.0) hp = sgn * fmin(2.0 * fabs(hp), a.k.rk_hmax);
+    if (r == STATUS_DELETED) { st = (uint8_t)r; break; }
+  }
+  return done;
+}
+
 // Scalar fields sampled at a particle's state into its variables (the
 // sample behaviour).  Sampling after every step and sampling once at the end
 // of a chunk give the same variables: each sample overwrites the last, and
@@ -358,7 +478,15 @@ __device__ __forceinline__ unsigned long long advance_particle(const A &a, int64
     const double sgn = a.dt > 0.0 ? 1.0 : -1.0;
     Clock ck;
     ck.dt = a.dt; ck.k = 0; ck.d = 0.f;
-    if constexpr (sizeof(Real) == 8) {
+    bool adaptive = false;
+    if constexpr (X) adaptive = a.k.scheme == 2;
+    if (adaptive) {
+      if constexpr (X) {
+        double hp = a.p.hstep[p];
+        done = rkf45_steps<EXT>(a, c, lon, lat, dep, t, stp, hp, age, st, idp);
+        a.p.hstep[p] = hp;
+      }
+    } else if constexpr (sizeof(Real) == 8) {
       // FP64: the definition's loop, time accumulated step by step.
       while (sgn * (a.t_stop - t) > 0.0 && sgn * (a.t_end - t) > 0.0) {
         double h = a.dt;

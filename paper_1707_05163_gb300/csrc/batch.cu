@@ -245,8 +245,9 @@ extern "C" pg_status pg_execute_batch(int nrel, pg_pset *const *psets,
     return PG_ERR_UNSUPPORTED;
   }
   for (int r = 0; r < nrel; ++r)
-    if (kernels[r]->beh & (PG_SETTLE | PG_AGE | PG_SAMPLE)) {
-      set_error("batched execution runs advection, Brownian motion and sinking only (release %d)", r);
+    if ((kernels[r]->beh & (PG_SETTLE | PG_AGE | PG_SAMPLE)) || kernels[r]->scheme == PG_RKF45) {
+      set_error("batched execution runs RK4 or Euler advection, Brownian motion and sinking "
+                "only (release %d)", r);
       return PG_ERR_UNSUPPORTED;
     }
   if (fs->streaming || fs->nt < 1) {

@@ -200,6 +200,7 @@ pg_status alloc_arrays(PsetArrays &A, int pos, int64_t cap, int nvar) {
   al((void **)&A.step, n * 4);
   al((void **)&A.status, n);
   al((void **)&A.age, n * 8);
+  al((void **)&A.hstep, n * 8);
   if (nvar > 0) al((void **)&A.var, n * 8 * (size_t)nvar);
   if (e != cudaSuccess) {
     A.free_all();
@@ -231,6 +232,7 @@ std::vector<std::pair<void *, size_t>> state_arrays(const PsetArrays &A, int pos
     v = {{A.x, el}, {A.y, el}, {A.z, el}, {A.time, 8}, {A.id, 8}, {A.step, 4}, {A.status, 1}};
   }
   v.push_back({A.age, 8});
+  v.push_back({A.hstep, 8});
   for (int j = 0; j < nvar; ++j) v.push_back({A.var ? A.var + (size_t)j * cap : nullptr, 8});
   return v;
 }
@@ -277,7 +279,7 @@ PsetArrays pg::pset_arrays(const pg_pset *ps) {
   A.ci = ps->ci; A.cj = ps->cj; A.ck = ps->ck;
   A.fx = ps->fx; A.fy = ps->fy; A.fz = ps->fz;
   A.time = ps->time; A.id = ps->id; A.step = ps->step; A.status = ps->status;
-  A.age = ps->age; A.var = ps->var;
+  A.age = ps->age; A.var = ps->var; A.hstep = ps->hstep;
   return A;
 }
 
@@ -286,7 +288,7 @@ void pg::pset_set_arrays(pg_pset *ps, const PsetArrays &A) {
   ps->ci = A.ci; ps->cj = A.cj; ps->ck = A.ck;
   ps->fx = A.fx; ps->fy = A.fy; ps->fz = A.fz;
   ps->time = A.time; ps->id = A.id; ps->step = A.step; ps->status = A.status;
-  ps->age = A.age; ps->var = A.var;
+  ps->age = A.age; ps->var = A.var; ps->hstep = A.hstep;
 }
 
 namespace {
@@ -453,7 +455,8 @@ pg_status init_variables(pg_pset *ps, int64_t off, int64_t n, cudaStream_t st) {
   if (n <= 0) return PG_OK;
   const int sm = ps->fs->sm_count;
   fill_f64_kernel<<<grid_for(n, sm), 256, 0, st>>>(ps->age + off, 0.0, n);
-  note_launches(1);
+  fill_f64_kernel<<<grid_for(n, sm), 256, 0, st>>>(ps->hstep + off, 0.0, n);
+  note_launches(2);
   for (int j = 0; j < ps->nvar; ++j) {
     fill_f64_kernel<<<grid_for(n, sm), 256, 0, st>>>(ps->var + (size_t)j * ps->cap + off,
                                                      std::numeric_limits<double>::quiet_NaN(), n);
@@ -491,6 +494,16 @@ pg_status resolve_kernel(const pg_kernel *k, const pg_fieldset *fs, uint64_t see
   if (std::isnan(a.w_sink)) a.w_sink = 0.0;
   if ((k->beh & PG_SETTLE) && !constant("dwelling_depth", a.dwell)) return PG_ERR_STATE;
   if ((k->beh & PG_AGE) && !constant("max_age", a.max_age)) return PG_ERR_STATE;
+  if (k->scheme == PG_RKF45) {
+    if (!constant("rkf45_tol", a.rk_tol)) return PG_ERR_STATE;
+    auto lo = fs->constants.find("rkf45_min_dt"), hi = fs->constants.find("rkf45_max_dt");
+    a.rk_hmin = lo != fs->constants.end() ? lo->second : 1.0;
+    a.rk_hmax = hi != fs->constants.end() ? hi->second : 0.0;   // 0: the execute's |dt|
+    if (!(a.rk_tol > 0.0) || !(a.rk_hmin > 0.0) || a.rk_hmax < 0.0) {
+      set_error("RKF45 needs rkf45_tol > 0, rkf45_min_dt > 0, rkf45_max_dt >= 0");
+      return PG_ERR_ARG;
+    }
+  }
   if (!(a.kh >= 0.0)) {
     set_error("Kh must be >= 0");
     return PG_ERR_ARG;
@@ -669,36 +682,54 @@ pg_status pg_fieldset_stream(pg_fieldset *fs, const void *const *ptrs, pg_snapsh
   ARG(src_dtype == PG_F64 || src_dtype == PG_F32, "src_dtype must be PG_F64 or PG_F32");
   if (ptrs)
     for (int s = 0; s < fs->nt; ++s) ARG(ptrs[s] != nullptr, "every snapshot pointer must be set");
-  free_streaming(fs);
-  free_resident(fs);
-  fs->slabs.assign((size_t)fs->nt, nullptr);
   const size_t el = src_dtype == PG_F64 ? 8 : 4;
   const size_t bytes = (size_t)fs->nfields * fs->nodes * el;
+  // everything new is allocated first; the field set changes only once all
+  // of it is in place (a failure leaves it as it was)
+  std::vector<Slot> ring(fs->slot.size());
+  void *stage = nullptr, *pinned = nullptr;
+  cudaStream_t side = nullptr;
+  cudaEvent_t stage_free = nullptr;
   cudaError_t e = cudaSuccess;
-  for (auto &sl : fs->slot) {
+  for (auto &sl : ring) {
     if (e == cudaSuccess) e = dev_alloc(&sl.buf, fs->slab_bytes);
     if (e == cudaSuccess) e = dev_alloc((void **)&sl.scales, 4 * sizeof(float));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.free, cudaEventDisableTiming);
     sl.s = -1;
   }
-  if (e == cudaSuccess && fs->stage_bytes < bytes) {
-    dev_free(fs->d_stage);
-    fs->d_stage = nullptr;
-    fs->stage_bytes = 0;
-    e = dev_alloc(&fs->d_stage, bytes);
-    if (e == cudaSuccess) fs->stage_bytes = bytes;
-  }
-  if (e == cudaSuccess && cb) e = cudaMallocHost(&fs->h_pinned, bytes);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fs->side, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fs->stage_free, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventRecord(fs->stage_free, fs->side);
+  if (e == cudaSuccess && fs->stage_bytes < bytes) e = dev_alloc(&stage, bytes);
+  if (e == cudaSuccess && cb) e = cudaMallocHost(&pinned, bytes);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&stage_free, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(stage_free, side);
   if (e != cudaSuccess) {
-    free_streaming(fs);
+    for (auto &sl : ring) {
+      dev_free(sl.buf);
+      dev_free(sl.scales);
+      if (sl.ready) cudaEventDestroy(sl.ready);
+      if (sl.free) cudaEventDestroy(sl.free);
+    }
+    dev_free(stage);
+    if (pinned) cudaFreeHost(pinned);
+    if (side) cudaStreamDestroy(side);
+    if (stage_free) cudaEventDestroy(stage_free);
     cudaGetLastError();
     set_error("streaming setup failed: %s", cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? PG_ERR_NOMEM : PG_ERR_CUDA;
   }
+  free_streaming(fs);
+  free_resident(fs);
+  fs->slabs.assign((size_t)fs->nt, nullptr);
+  fs->slot = ring;
+  if (stage) {
+    dev_free(fs->d_stage);
+    fs->d_stage = stage;
+    fs->stage_bytes = bytes;
+  }
+  fs->h_pinned = pinned;
+  fs->side = side;
+  fs->stage_free = stage_free;
   fs->streaming = true;
   fs->cb = cb;
   fs->cb_user = user;
@@ -856,7 +887,8 @@ pg_status pg_kernel_create(int scheme, unsigned behaviours, double kh, double w_
                            pg_kernel **out) {
   clear_error();
   ARG(out, "out must not be NULL");
-  ARG(scheme == PG_EULER || scheme == PG_RK4, "scheme must be PG_EULER or PG_RK4");
+  ARG(scheme == PG_EULER || scheme == PG_RK4 || scheme == PG_RKF45,
+      "scheme must be PG_EULER, PG_RK4 or PG_RKF45");
   ARG((behaviours & ~(PG_BROWNIAN | PG_SINK | PG_SETTLE | PG_AGE | PG_SAMPLE)) == 0,
       "unknown behaviour bits");
   ARG(std::isnan(kh) || (std::isfinite(kh) && kh >= 0.0), "kh must be NaN, or finite and >= 0");
@@ -1016,6 +1048,7 @@ pg_status pg_pset_add(pg_pset *ps, int64_t n, const double *lon, const double *l
     cp(B.time, A.time, m * 8); cp(B.id, A.id, m * 8); cp(B.step, A.step, m * 4);
     cp(B.status, A.status, m);
     cp(B.age, A.age, m * 8);
+    cp(B.hstep, A.hstep, m * 8);
     for (int j = 0; j < ps->nvar; ++j)
       cp(B.var + (size_t)j * cap, A.var + (size_t)j * ps->cap, m * 8);
     if (e != cudaSuccess) {
@@ -1184,6 +1217,28 @@ static pg_status deliver_output(pg_pset *ps, int k, pg_output_cb out, pg_record_
 static pg_status execute_impl(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
                               double output_dt, pg_output_cb out, pg_record_cb rec, int indexed,
                               void *user, void *stream, int64_t *steps_done);
+static pg_status execute_loop(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
+                              double output_dt, pg_output_cb out, pg_record_cb rec, int indexed,
+                              void *user, void *stream, int64_t *steps_done, bool &ran);
+
+// The time range of the alive particles from their device state (after an
+// execute that stopped part-way); unchanged when none is alive.
+static void refresh_time_range(pg_pset *ps, cudaStream_t st) {
+  const int64_t n = ps->n;
+  if (n == 0) return;
+  std::vector<double> t((size_t)n);
+  std::vector<uint8_t> stat((size_t)n);
+  if (cudaStreamSynchronize(st) != cudaSuccess ||
+      cudaMemcpy(t.data(), ps->time, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(stat.data(), ps->status, n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  double lo = std::numeric_limits<double>::infinity(), hi = -lo;
+  for (int64_t i = 0; i < n; ++i)
+    if (stat[i] == 0) { lo = std::min(lo, t[i]); hi = std::max(hi, t[i]); }
+  if (lo <= hi) { ps->t_min = lo; ps->t_max = hi; }
+}
 
 pg_status pg_execute(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
                      double output_dt, pg_output_cb out, void *user, void *stream,
@@ -1204,6 +1259,21 @@ pg_status pg_execute_records(pg_pset *ps, const pg_kernel *k, double runtime, do
 static pg_status execute_impl(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
                               double output_dt, pg_output_cb out, pg_record_cb rec, int indexed,
                               void *user, void *stream, int64_t *steps_done) {
+  bool ran = false;
+  const pg_status r = execute_loop(ps, k, runtime, dt, output_dt, out, rec, indexed, user, stream,
+                                   steps_done, ran);
+  if (r && ran) {
+    // stopped part-way: the next execute starts from where the particles are
+    const std::string msg = pg_last_error();
+    refresh_time_range(ps, (cudaStream_t)stream);
+    set_error("%s", msg.c_str());
+  }
+  return r;
+}
+
+static pg_status execute_loop(pg_pset *ps, const pg_kernel *k, double runtime, double dt,
+                              double output_dt, pg_output_cb out, pg_record_cb rec, int indexed,
+                              void *user, void *stream, int64_t *steps_done, bool &ran) {
   ARG(ps && k, "particle set and kernel must not be NULL");
   ARG(std::isfinite(runtime) && runtime >= 0.0, "runtime must be finite and >= 0");
   ARG(std::isfinite(dt) && dt != 0.0, "dt must be finite and non-zero");
@@ -1245,15 +1315,18 @@ static pg_status execute_impl(pg_pset *ps, const pg_kernel *k, double runtime, d
     pg_status r = resolve_kernel(k, fs, ps->seed, a.k);
     if (r) return r;
   }
-  const bool ext = (k->beh & (PG_SETTLE | PG_AGE | PG_SAMPLE)) || fs->interp != PG_LINEAR;
+  if (k->scheme == PG_RKF45 && a.k.rk_hmax == 0.0) a.k.rk_hmax = std::fabs(dt);
+  if (k->scheme == PG_RKF45) a.k.rk_hmin = std::min(a.k.rk_hmin, a.k.rk_hmax);
+  const bool ext = (k->beh & (PG_SETTLE | PG_AGE | PG_SAMPLE)) || fs->interp != PG_LINEAR ||
+                   k->scheme == PG_RKF45;
   if (ext && ps->pos == PG_POS_CELL) {
-    set_error("the settle, age and sample behaviours and nearest-neighbour interpolation need "
-              "lon/lat/depth positions");
+    set_error("RKF45, the settle, age and sample behaviours and nearest-neighbour "
+              "interpolation need lon/lat/depth positions");
     return PG_ERR_UNSUPPORTED;
   }
   if (ext && ps->pos == PG_POS_F32 && fs->storage != PG_F32) {
-    set_error("the settle, age and sample behaviours and nearest-neighbour interpolation need "
-              "FP32 or FP64 field storage");
+    set_error("RKF45, the settle, age and sample behaviours and nearest-neighbour "
+              "interpolation need FP32 or FP64 field storage");
     return PG_ERR_UNSUPPORTED;
   }
   if (k->beh & PG_SAMPLE) {
@@ -1351,8 +1424,9 @@ static pg_status execute_impl(pg_pset *ps, const pg_kernel *k, double runtime, d
     a.p.n = n_active;
     a.p.x = ps->x; a.p.y = ps->y; a.p.z = ps->z;
     a.p.time = ps->time; a.p.id = ps->id; a.p.step = ps->step; a.p.status = ps->status;
-    a.p.age = ps->age; a.p.var = ps->var; a.p.vstride = ps->cap;
+    a.p.age = ps->age; a.p.var = ps->var; a.p.vstride = ps->cap; a.p.hstep = ps->hstep;
     a.t_stop = tn;
+    a.t_clip = next_out;
     if (ps->timing) {
       if (ps->ev_used + 2 > ps->ev.size()) {
         for (int q = 0; q < 2; ++q) {
@@ -1365,6 +1439,7 @@ static pg_status execute_impl(pg_pset *ps, const pg_kernel *k, double runtime, d
     }
     a.p.ci = ps->ci; a.p.cj = ps->cj; a.p.ck = ps->ck;
     a.p.fx = ps->fx; a.p.fy = ps->fy; a.p.fz = ps->fz;
+    ran = true;
     if (ps->pos == PG_POS_CELL) CU(launch_advect_cell(a, fs->storage, ps->tune.block, st));
     else CU(launch_advect_plain(a, ps->pos, fs->storage, ps->tune.block, st));
     if (ps->timing) {

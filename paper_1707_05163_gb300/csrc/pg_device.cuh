@@ -60,6 +60,7 @@ struct KernArgs {
   float deg_m_f, inv_deg_m_f, kh_f, w_sink_f;   // FP32 copies for the FP32 path
   double dwell = 0.0, max_age = 0.0;   // settle: dwelling depth (m); age: deletion age (s)
   float dwell_f = 0.f;
+  double rk_tol = 0.0, rk_hmin = 0.0, rk_hmax = 0.0;   // RKF45: metres, seconds, seconds
 };
 
 // Behaviour bits of the worked example (Sect. 3), beside Brownian (1) and
@@ -79,6 +80,7 @@ struct PartArgs {
   double *age = nullptr;     // [n] seconds of age (age behaviour)
   double *var = nullptr;     // [ntr][vstride] sampled variables (sample behaviour)
   int64_t vstride = 0;
+  double *hstep = nullptr;   // [n] RKF45 step lengths (0: start from dt)
 };
 
 // Mesh geometry of a kernel instantiation: runtime (GEO_ANY, the FP64 path)
@@ -102,6 +104,7 @@ struct StepArgs {
   KernArgs k;
   PartArgs p;
   double dt, t_stop, t_end;
+  double t_clip;                    // RKF45 steps land on this time (next output) and t_end
   unsigned long long *steps_done;   // particle-steps taken (device counter)
   int *err;                         // first DevErr recorded (device word)
 };

@@ -44,8 +44,9 @@ struct PsetArrays {
   uint8_t *status = nullptr;
   double *age = nullptr;      // [cap]
   double *var = nullptr;      // [nvar][cap] sampled variables
+  double *hstep = nullptr;    // [cap] RKF45 step lengths
   void free_all() {
-    void *ps[] = {x, y, z, ci, cj, ck, fx, fy, fz, time, id, step, status, age, var};
+    void *ps[] = {x, y, z, ci, cj, ck, fx, fy, fz, time, id, step, status, age, var, hstep};
     for (void *p : ps) dev_free(p);
     *this = PsetArrays();
   }
@@ -161,6 +162,7 @@ struct pg_pset {
   uint8_t *status = nullptr;
   double *age = nullptr;               // [cap] age in seconds (age behaviour)
   double *var = nullptr;               // [nvar][cap] sampled variables
+  double *hstep = nullptr;             // [cap] RKF45 step lengths (0: start from dt)
   int nvar = 0;                        // the field set's scalar fields at creation
   double t_min = 0.0, t_max = 0.0;     // range of particle times
   pg_tune tune{256, 0, 64};

@@ -292,10 +292,11 @@ cudaError_t launch_resort(pg_pset *ps, cudaStream_t st, int64_t *n_alive) {
   gather_kernel<uint32_t><<<gr, 256, 0, st>>>(ps->step, B.step, perm, n);
   gather_kernel<uint8_t><<<gr, 256, 0, st>>>(ps->status, B.status, perm, n);
   gather_kernel<double><<<gr, 256, 0, st>>>(ps->age, B.age, perm, n);
+  gather_kernel<double><<<gr, 256, 0, st>>>(ps->hstep, B.hstep, perm, n);
   for (int j = 0; j < ps->nvar; ++j)
     gather_kernel<double><<<gr, 256, 0, st>>>(ps->var + (size_t)j * ps->cap,
                                               B.var + (size_t)j * ps->cap, perm, n);
-  note_launches((ps->pos == PG_POS_CELL ? 11 : 8) + 1 + ps->nvar);
+  note_launches((ps->pos == PG_POS_CELL ? 11 : 8) + 2 + ps->nvar);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (!n_alive) {
     // fixed-pointer mode: copy the sorted arrays back in place
@@ -311,7 +312,8 @@ cudaError_t launch_resort(pg_pset *ps, cudaStream_t st, int64_t *n_alive) {
         (e = cudaMemcpyAsync(ps->id, B.id, (size_t)n * 8, cudaMemcpyDeviceToDevice, st)) ||
         (e = cudaMemcpyAsync(ps->step, B.step, (size_t)n * 4, cudaMemcpyDeviceToDevice, st)) ||
         (e = cudaMemcpyAsync(ps->status, B.status, (size_t)n, cudaMemcpyDeviceToDevice, st)) ||
-        (e = cudaMemcpyAsync(ps->age, B.age, (size_t)n * 8, cudaMemcpyDeviceToDevice, st)))
+        (e = cudaMemcpyAsync(ps->age, B.age, (size_t)n * 8, cudaMemcpyDeviceToDevice, st)) ||
+        (e = cudaMemcpyAsync(ps->hstep, B.hstep, (size_t)n * 8, cudaMemcpyDeviceToDevice, st)))
       return e;
     for (int j = 0; j < ps->nvar; ++j)
       if ((e = cudaMemcpyAsync(ps->var + (size_t)j * ps->cap, B.var + (size_t)j * ps->cap,

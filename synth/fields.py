@@ -26,7 +26,8 @@ __all__ = [
     "FLAT", "SPHERICAL", "DAY", "FieldSpec", "GlobalField", "solid_body_rotation",
     "zonal_flow_sphere", "oscillating_flow", "peninsula", "peninsula_psi",
     "stommel_gyre", "stommel_psi", "decaying_eddy", "eddy_trajectory", "zero_field",
-    "uniform_flow", "linear_field", "global_axes", "temperature",
+    "uniform_flow", "linear_field", "global_axes", "temperature", "temperature_base",
+    "temperature_at",
 ]
 
 
@@ -351,6 +352,30 @@ def _global_base2d_torch(self, s, device):
 
 
 GlobalField.base2d_torch = _global_base2d_torch
+
+
+def temperature_base(lon, lat, depth, seed=9, noise=0.5, dtype=np.float64):
+    """The time-independent part of :func:`temperature`, (nz, ny, nx)."""
+    rng = np.random.default_rng(seed)
+    lon = np.asarray(lon, np.float64)
+    lat = np.asarray(lat, np.float64)
+    depth = np.asarray(depth, np.float64)
+    if np.max(np.abs(lat)) > 90.0:
+        latd = -60.0 + 120.0 * (lat - lat.min()) / max(lat.max() - lat.min(), 1.0)
+    else:
+        latd = lat
+    base = (2.0 + 26.0 * np.cos(np.deg2rad(latd))[None, :, None] ** 2 *
+            np.exp(-depth / 700.0)[:, None, None]).astype(dtype)
+    out = np.empty((len(depth), len(latd), len(lon)), dtype)
+    out[...] = base
+    out += (rng.standard_normal(size=out.shape, dtype=np.float32 if dtype == np.float32
+                                else np.float64) * noise).astype(dtype)
+    return out
+
+
+def temperature_at(base, t, period=30 * DAY):
+    """Snapshot of :func:`temperature` at time t from its base."""
+    return base + base.dtype.type(np.sin(2 * np.pi * t / period))
 
 
 def temperature(lon, lat, depth, times, seed=9, period=30 * DAY, noise=0.5):

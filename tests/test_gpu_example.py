@@ -278,3 +278,106 @@ def test_example_error_conventions(pg):
     with pytest.raises(pg.PGError) as e:          # not in the batched form
         pg.execute_batch([pb], [pg.Kernel("rk4", ("age",))], [DAY], [600.0], tune=(64, 0))
     assert e.value.code == -8
+
+
+# ------------------------------------------------------------------ RKF45
+
+def _rkf_oracle(spec, lon, lat, dep, t0, dt, T, out_dt, tol, hmin, hmax, data=None):
+    f = O.Field(spec.lon, spec.lat, spec.depth, spec.times,
+                spec.data if data is None else data, spec.mesh, spec.periodic_lon, spec.period)
+    n = len(lon)
+    st = dict(lon=np.array(lon, np.float64), lat=np.array(lat, np.float64),
+              depth=np.zeros(n) if dep is None else np.array(dep, np.float64),
+              time=np.full(n, t0), ids=np.arange(n, dtype=np.uint64),
+              step=np.zeros(n, np.uint32), status=np.zeros(n, np.uint8))
+    hstep = np.zeros(n)
+    k = O.Kernel(O.RKF45, rk45_tol=tol, rk45_hmin=hmin, rk45_hmax=hmax)
+    sgn = np.sign(dt)
+    t_end = t0 + sgn * T
+    stops = []
+    m = 1
+    while out_dt > 0 and sgn * (t_end - (t0 + sgn * m * out_dt)) > 0:
+        stops.append(t0 + sgn * m * out_dt)
+        m += 1
+    stops.append(t_end)
+    outs, total = {}, 0
+    for ts in stops:
+        total += O.run(f, k, st["lon"], st["lat"], st["depth"], st["time"], st["ids"], st["step"],
+                       st["status"], dt, ts, t_end, hstep=hstep)
+        outs[ts] = {kk: v.copy() for kk, v in st.items()}
+    st["steps"] = total
+    return st, outs
+
+
+@pytest.mark.parametrize("dt", [3600.0, -3600.0])
+def test_rkf45_fp64_bit_identical_with_outputs(pg, dt):
+    """Adaptive RKF45 on the steady Stommel gyre (flat, FP64): steps adapt to
+    the western boundary current; positions, statuses, step counts and times
+    equal the oracle's bit for bit at every output time, with launches of
+    seven steps and re-sorts on the way (the results do not depend on them)."""
+    spec = synth.stommel_gyre(n=101)
+    rng = np.random.default_rng(61)
+    n = 3000
+    lon = rng.uniform(1e4, 9.9e5, n)
+    lat = rng.uniform(1e4, 9.9e5, n)
+    T, out = 10 * DAY, 2.5 * DAY
+    tol, hmin, hmax = 2e-4, 60.0, 4 * 3600.0
+    t0 = 0.0 if dt > 0 else 10 * DAY
+    o, outs = _rkf_oracle(spec, lon, lat, None, t0, dt, T, out, tol, hmin, hmax)
+    fs = pg.FieldSet.from_spec(spec, storage="f64")
+    fs.add_constant("rkf45_tol", tol)
+    fs.add_constant("rkf45_min_dt", hmin)
+    fs.add_constant("rkf45_max_dt", hmax)
+    ps = pg.ParticleSet(fs, lon, lat, t0=t0, pos="f64")
+    ps.set_tune(block=128, resort_steps=5, chunk_steps=7)
+    got = {}
+    steps = ps.execute_records(pg.Kernel("rkf45"), T, dt, out,
+                               lambda t, r: got.__setitem__(t, r), indexed=False)
+    assert steps == o["steps"]
+    g = ps.get()
+    for k in ("lon", "lat", "status", "step", "time"):
+        np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+    assert sorted(got) == sorted(outs)
+    for t, r in got.items():
+        order = np.argsort(r["id"])
+        for k in ("lon", "lat", "status"):
+            np.testing.assert_array_equal(r[k][order], outs[t][k], err_msg=f"{k} t={t}")
+    # the steps adapted: far fewer than fixed 1-minute steps, more than 4-hour ones
+    alive = o["status"] == 0
+    per = o["step"][alive] / (T / 3600.0)
+    assert per.min() < 0.5 and per.max() > 1.0, (per.min(), per.max())
+
+
+def test_rkf45_fp32_global_3d(pg):
+    """FP32 positions (extended kernel) on the time-dependent global 3-D
+    field: within the FP32 tolerance of the oracle; launches and re-sorts do
+    not change the result."""
+    gf = synth.GlobalField(res_deg=2.0, nz=8, nt=4, seed=27, kmax=20, period=4 * DAY)
+    spec = gf.spec(materialise=True)
+    lon, lat, dep = synth.uniform_particles(3000, 31, (0, 360), (-70, 70), (6.0, 900.0),
+                                            dtype=np.float32)
+    T = 3 * DAY
+    tol, hmin, hmax = 20.0, 60.0, 7200.0
+    o, _ = _rkf_oracle(spec, lon, lat, dep, 0.0, 1800.0, T, 0.0, tol, hmin, hmax)
+    fs = pg.FieldSet.from_spec(spec, storage="f32")
+    fs.add_constant("rkf45_tol", tol)
+    fs.add_constant("rkf45_min_dt", hmin)
+    fs.add_constant("rkf45_max_dt", hmax)
+    res = []
+    for tune in (None, (64, 3, 5)):
+        ps = pg.ParticleSet(fs, lon, lat, dep, pos="f32")
+        if tune:
+            ps.set_tune(*tune)
+        ps.execute(pg.Kernel("rkf45"), T, 1800.0)
+        res.append(ps.get())
+    for k in ("lon", "lat", "depth", "status", "step", "time"):
+        np.testing.assert_array_equal(res[0][k], res[1][k], err_msg=k)
+    g = res[0]
+    np.testing.assert_array_equal(g["status"], o["status"])
+    alive = o["status"] == 0
+    # FP32 and FP64 error estimates may decide a trial differently now and
+    # then: step counts agree for most particles, positions within cells
+    assert np.mean(g["step"] == o["step"]) > 0.9, np.mean(g["step"] == o["step"])
+    e = cell_error(g, o, spec)[alive]
+    assert np.mean(e) < 1e-3 and np.max(e) < 2e-2, (np.mean(e), np.max(e))
+    np.testing.assert_array_equal(g["time"][alive], np.full(alive.sum(), T))

@@ -23,10 +23,13 @@ def pg():
 
 
 def _gyre_case(n, seed):
+    """The Stommel gyre with an eastward drift of 0.3 m/s added, so that
+    particles leave through the eastern boundary during the run."""
     spec = synth.stommel_gyre(n=101)
+    spec.data = spec.data.copy()
+    spec.data[:, 0] += 0.3
     rng = np.random.default_rng(seed)
     L = 1e6
-    # some particles start near the boundaries and leave the domain
     lon = rng.uniform(0.0, L, n)
     lat = rng.uniform(0.0, L, n)
     return spec, lon, lat
@@ -66,7 +69,7 @@ def test_records_against_oracle_fp64(pg, indexed):
             np.testing.assert_array_equal(r[k][order], ref[k][want], err_msg=f"{k} t={t}")
         prev = ref["status"]
     final = o["final"]["status"]
-    assert (final != 0).sum() > 1000 and (final == 0).sum() > 100_000
+    assert (final != 0).sum() > 10_000 and (final == 0).sum() > 100_000
 
 
 def test_records_carry_variables_and_cell_positions(pg):
@@ -116,7 +119,7 @@ def test_records_carry_variables_and_cell_positions(pg):
     np.testing.assert_array_equal(last["status"][o], gs["status"][ids])
     seen = np.concatenate([recs[t]["id"] for t in sorted(recs)])
     assert len(np.unique(seen)) == m               # every particle appears
-    assert (v["age"] <= 1.5 * DAY).all() and (gs["status"] == 4).sum() > 1000
+    assert (v["age"] <= 1.5 * DAY).all() and (gs["status"] == 4).sum() > 300
 
 
 def test_failing_record_hook(pg):
