@@ -636,7 +636,7 @@ def example_or_rkf45_workload(args, rank, world, local):
         g = ps.get() if timed else None
         v = ps.get_variables() if (timed and example) else None
         ps.destroy()
-        return steps.value, ev0.elapsed_time(ev1), kms.value, g, v
+        return steps.value, ev0.elapsed_time(ev1), kms.value, g, v, tuple(rows)
 
     for _ in range(max(1, args.warmup)):
         run(kern, dt, False)
@@ -647,7 +647,7 @@ def example_or_rkf45_workload(args, rank, world, local):
         if best is None or r[1] < best[1]:
             best = r
     clk = clocks.stop()
-    steps, ms, kms, g, v = best
+    steps, ms, kms, g, v, rec = best
     plain = run(pg.Kernel("rk4"), -1800.0 if example else 1800.0, False)
     line = {
         "metric": METRIC, "value": steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
@@ -669,7 +669,7 @@ def example_or_rkf45_workload(args, rank, world, local):
     }
     if example:
         st = g["status"]
-        line["example"] = {"output_rows": rows[0], "outputs": rows[1],
+        line["example"] = {"output_rows": rec[0], "outputs": rec[1],
                            "deleted_by_age": int((st == 4).sum()), "alive": int((st == 0).sum()),
                            "out_of_domain": int(((st == 1) | (st == 2)).sum()),
                            "mean_lifespan_temperature_at_death_degC":

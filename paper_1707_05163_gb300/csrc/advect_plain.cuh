@@ -340,49 +340,79 @@ __device__ __forceinline__ int finish_step(const A &a, Real &lon, Real &lat, Rea
 
 // ------------------------------------------------------------------ RKF45
 // The Fehlberg 4(5) pair (Sect. 2.1.1 names Runge-Kutta-Fehlberg): stage
-// times, stage weights, fourth- and fifth-order weights.
-__device__ constexpr double kRkfC[6] = {0.0, 1.0 / 4.0, 3.0 / 8.0, 12.0 / 13.0, 1.0, 1.0 / 2.0};
-__device__ constexpr double kRkfA[6][5] = {
+// times, stage weights, fourth- and fifth-order weights, in FP64 and FP32.
+// Fourth- and fifth-order weights (read in unrolled code).
+__device__ constexpr double kRkfB4[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0,
+                                         -1.0 / 5.0, 0.0};
+__device__ constexpr double kRkfB5[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0,
+                                         28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+// Stage times and stage weights (read with the stage as a runtime index).
+__device__ constexpr double kRkfC64[6] = {0.0, 1.0 / 4.0, 3.0 / 8.0, 12.0 / 13.0, 1.0, 1.0 / 2.0};
+__device__ constexpr double kRkfA64[6][5] = {
     {0, 0, 0, 0, 0},
     {1.0 / 4.0, 0, 0, 0, 0},
     {3.0 / 32.0, 9.0 / 32.0, 0, 0, 0},
     {1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0, 0, 0},
     {439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0, 0},
     {-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0}};
-__device__ constexpr double kRkfB4[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0,
-                                         -1.0 / 5.0, 0.0};
-__device__ constexpr double kRkfB5[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0,
-                                         28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+__device__ constexpr float kRkfC32[6] = {0.0f, (float)(1.0 / 4.0), (float)(3.0 / 8.0),
+                                         (float)(12.0 / 13.0), 1.0f, 0.5f};
+__device__ constexpr float kRkfA32[6][5] = {
+    {0, 0, 0, 0, 0},
+    {(float)(1.0 / 4.0), 0, 0, 0, 0},
+    {(float)(3.0 / 32.0), (float)(9.0 / 32.0), 0, 0, 0},
+    {(float)(1932.0 / 2197.0), (float)(-7200.0 / 2197.0), (float)(7296.0 / 2197.0), 0, 0},
+    {(float)(439.0 / 216.0), -8.0f, (float)(3680.0 / 513.0), (float)(-845.0 / 4104.0), 0},
+    {(float)(-8.0 / 27.0), 2.0f, (float)(-3544.0 / 2565.0), (float)(1859.0 / 4104.0),
+     (float)(-11.0 / 40.0)}};
+__device__ __forceinline__ double rkf_c(int i, double) { return kRkfC64[i]; }
+__device__ __forceinline__ float rkf_c(int i, float) { return kRkfC32[i]; }
+__device__ __forceinline__ double rkf_a(int i, int j, double) { return kRkfA64[i][j]; }
+__device__ __forceinline__ float rkf_a(int i, int j, float) { return kRkfA32[i][j]; }
 
 // One trial of length h from (lon, lat, dep) at the clock's step start: the
 // fourth-order position x4 and the error estimate in metres (the largest
 // over the axes of |X5 - X4|, degrees turned into metres at the latitude of
-// X4 on a sphere).  Returns 0, a particle status, or -1 (internal failure).
+// X4 on a sphere).  The six stages run in a loop that is not unrolled (one
+// copy of the velocity code); each stage's slopes go to its own registers,
+// and the stage position adds h a_ij k_j over the earlier stages j in order
+// (later ones have zero weight and zero slopes, which add exactly zero).
+// Returns 0, a particle status, or -1 (internal failure).
 template <bool EXT, typename Real, typename Store, int NF, bool D3, int GEO, class A>
 __device__ __forceinline__ int rkf45_trial(const A &a, Sampler<Real, Store, NF, D3, GEO> &c,
                                            Clock &ck, Real lon, Real lat, Real dep, Real h,
                                            Real (&x4)[3], Real &err) {
-  Real k[6][3];
-  int r;
+  Real kx[6], ky[6], kz[6];
 #pragma unroll
+  for (int j = 0; j < 6; ++j) { kx[j] = (Real)0; ky[j] = (Real)0; kz[j] = (Real)0; }
+  int r;
+#pragma unroll 1
   for (int i = 0; i < 6; ++i) {
     Real px = lon, py = lat, pz = dep;
 #pragma unroll
-    for (int j = 0; j < i; ++j) {
-      px = px + h * (Real)kRkfA[i][j] * k[j][0];
-      py = py + h * (Real)kRkfA[i][j] * k[j][1];
-      pz = pz + h * (Real)kRkfA[i][j] * k[j][2];
+    for (int j = 0; j < 5; ++j) {
+      const Real ha = h * rkf_a(i, j, h);
+      px = px + ha * kx[j];
+      py = py + ha * ky[j];
+      pz = pz + ha * kz[j];
     }
-    if ((r = velocity<EXT>(a, c, ck, (Real)kRkfC[i] * h, px, py, pz, k[i]))) return r;
+    Real kn[3];
+    if ((r = velocity<EXT>(a, c, ck, rkf_c(i, h) * h, px, py, pz, kn))) return r;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (i == j) { kx[j] = kn[0]; ky[j] = kn[1]; kz[j] = kn[2]; }
+    }
   }
   Real d4[3] = {(Real)0, (Real)0, (Real)0}, d5[3] = {(Real)0, (Real)0, (Real)0};
 #pragma unroll
-  for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      d4[q] = d4[q] + (Real)kRkfB4[i] * k[i][q];
-      d5[q] = d5[q] + (Real)kRkfB5[i] * k[i][q];
-    }
+  for (int i = 0; i < 6; ++i) {
+    d4[0] = d4[0] + (Real)kRkfB4[i] * kx[i];
+    d4[1] = d4[1] + (Real)kRkfB4[i] * ky[i];
+    d4[2] = d4[2] + (Real)kRkfB4[i] * kz[i];
+    d5[0] = d5[0] + (Real)kRkfB5[i] * kx[i];
+    d5[1] = d5[1] + (Real)kRkfB5[i] * ky[i];
+    d5[2] = d5[2] + (Real)kRkfB5[i] * kz[i];
+  }
   x4[0] = lon + h * d4[0];
   x4[1] = lat + h * d4[1];
   x4[2] = dep + h * d4[2];

@@ -12,8 +12,11 @@
 // every tile is full in N and K; M may be ragged.
 //
 // GEMM engines: `gemm_nt_mma` uses warp-level mma.sync m16n8k16 (the
-// portable tensor-core path); the tcgen05 engine in mlp_tc.cu runs the
-// forward products on Blackwell's 5th-generation tensor cores when enabled.
+// portable tensor-core path); the tcgen05 engine in mlp_tc.cu runs, when
+// enabled, every product whose widths are 64 or 256 on Blackwell's
+// 5th-generation tensor cores: the forward (bias and GELU in the epilogue),
+// the input gradient (GELU' in the epilogue) and the weight gradient (a
+// split-K product over the batch).
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -353,6 +356,9 @@ struct pg_mlp {
   float *y = nullptr;                 // output [cap x pout] FP32
   float *dy = nullptr;                // FP32 gradient of the current layer output [cap x width]
   __nv_bfloat16 *dyb = nullptr, *dyt = nullptr, *xt = nullptr;   // BF16 grads, transposes
+  __nv_bfloat16 *dyb2 = nullptr;      // second BF16 gradient buffer (tcgen05 input gradient)
+  float *gscratch = nullptr;          // split-K partials of the weight gradient
+  size_t gscratch_bytes = 0;
   float *loss_partial = nullptr;
   int use_tc = 0;                     // tcgen05 forward when available
   int *d_err = nullptr;               // device word: tcgen05 wait gave up
@@ -362,7 +368,10 @@ namespace pg {
 cudaError_t gemm_nt_tc(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
                        int64_t M, int N, int K, const float *bias, int act, float *out_f32,
                        __nv_bfloat16 *out_bf16, __nv_bfloat16 *pre_bf16, int ldc, cudaStream_t st,
-                       int *err);
+                       int *err, const __nv_bfloat16 *gin = nullptr);
+cudaError_t gemm_tn_splitk_tc(const __nv_bfloat16 *A, int64_t lda, int Mrows,
+                              const __nv_bfloat16 *B, int64_t ldb, int N, int64_t K, float *out,
+                              float *scratch, size_t scratch_bytes, cudaStream_t st, int *err);
 }
 
 namespace {
@@ -374,6 +383,8 @@ void free_ws(pg_mlp *n) {
   n->act.clear();
   n->pre.clear();
   dev_free(n->y); dev_free(n->dy); dev_free(n->dyb); dev_free(n->dyt); dev_free(n->xt);
+  dev_free(n->dyb2); dev_free(n->gscratch);
+  n->dyb2 = nullptr; n->gscratch = nullptr; n->gscratch_bytes = 0;
   dev_free(n->loss_partial);
   n->x0 = nullptr; n->y = nullptr; n->dy = nullptr; n->dyb = nullptr; n->dyt = nullptr;
   n->xt = nullptr; n->loss_partial = nullptr;
@@ -400,6 +411,10 @@ cudaError_t ensure_ws(pg_mlp *n, int64_t rows) {
   al((void **)&n->y, cap * n->pout * 4);
   al((void **)&n->dy, cap * wmax * 4);
   al((void **)&n->dyb, cap * wmax * 2);
+  al((void **)&n->dyb2, cap * wmax * 2);
+  // split-K partials: up to 64 splits of a 256 x 256 product
+  n->gscratch_bytes = (size_t)64 * 256 * 256 * sizeof(float);
+  al((void **)&n->gscratch, n->gscratch_bytes);
   al((void **)&n->dyt, cap * wmax * 2);
   al((void **)&n->xt, cap * std::max(n->width, n->pin) * 2);
   al((void **)&n->loss_partial, 1024 * 4);
@@ -472,19 +487,33 @@ cudaError_t backward(pg_mlp *n, int64_t rows, cudaStream_t st) {
     dim3 g2((din + 31) / 32, (unsigned)((rows + 31) / 32));
     transpose_bf16<<<g2, dim3(32, 8), 0, st>>>(X, (int)rows, din, din, n->xt, (int)rows);
     note_launches(3);
+    const bool tc = n->use_tc && (din == 64 || din == 256) && (dout == 64 || dout == 256);
     // rows must be a multiple of 32 for the K loop; the batch is padded
-    if ((e = gemm_nt(n->dyt, (int)rows, n->xt, (int)rows, dout, din, (int)rows, nullptr, 0,
-                     n->g + n->woff[l], nullptr, nullptr, din, 0, st)) != cudaSuccess)
-      return e;
+    if (tc) e = gemm_tn_splitk_tc(n->dyt, rows, dout, n->xt, rows, din, rows, n->g + n->woff[l],
+                                  n->gscratch, n->gscratch_bytes, st, n->d_err);
+    else e = gemm_nt(n->dyt, (int)rows, n->xt, (int)rows, dout, din, (int)rows, nullptr, 0,
+                     n->g + n->woff[l], nullptr, nullptr, din, 0, st);
+    if (e != cudaSuccess) return e;
     if (l == 0) break;
-    // dX [rows x din] = dPre W  (B = W^T [din x dout])
-    if ((e = gemm_nt(n->dyb, dout, n->wbt + n->woff[l], dout, rows, din, dout, nullptr, 0, n->dy,
-                     nullptr, nullptr, din, 0, st)) != cudaSuccess)
-      return e;
-    // through the GELU of layer l-1
-    gelu_backward<<<grid1(rows * din), 256, 0, st>>>(n->dy, n->pre[l - 1], rows, din, n->dyb,
-                                                     n->dy);
-    note_launches(1);
+    if (tc) {
+      // dPre of layer l-1 = (dPre W) * GELU'(pre) in one product (B = W^T
+      // [din x dout]); FP32 into dy, BF16 into the other buffer (the one
+      // read as A must not be overwritten by other tiles)
+      if ((e = gemm_nt_tc(n->dyb, dout, n->wbt + n->woff[l], dout, rows, din, dout, nullptr, 2,
+                          n->dy, n->dyb2, nullptr, din, st, n->d_err, n->pre[l - 1])) !=
+          cudaSuccess)
+        return e;
+      std::swap(n->dyb, n->dyb2);
+    } else {
+      // dX [rows x din] = dPre W  (B = W^T [din x dout])
+      if ((e = gemm_nt(n->dyb, dout, n->wbt + n->woff[l], dout, rows, din, dout, nullptr, 0, n->dy,
+                       nullptr, nullptr, din, 0, st)) != cudaSuccess)
+        return e;
+      // through the GELU of layer l-1
+      gelu_backward<<<grid1(rows * din), 256, 0, st>>>(n->dy, n->pre[l - 1], rows, din, n->dyb,
+                                                       n->dy);
+      note_launches(1);
+    }
     wcur = din;
   }
   return cudaGetLastError();
@@ -661,6 +690,15 @@ static pg_status mlp_grad_impl(pg_mlp *n, const float *x, const float *t, int64_
   note_launches(1);
   CUM(cudaMemsetAsync(n->g, 0, n->nparam * 4, st));
   CUM(backward(n, M, st));
+  if (n->use_tc) {
+    int err = 0;
+    CUM(cudaMemcpyAsync(&err, n->d_err, 4, cudaMemcpyDeviceToHost, st));
+    CUM(cudaStreamSynchronize(st));
+    if (err) {
+      set_error("a tcgen05 product gave up waiting for its accumulator");
+      return PG_ERR_TIMEOUT;
+    }
+  }
   if (loss) {
     std::vector<float> lp(nb);
     CUM(cudaMemcpyAsync(lp.data(), n->loss_partial, nb * 4, cudaMemcpyDeviceToHost, st));
