@@ -69,7 +69,8 @@ def parse():
     ap.add_argument("--train-steps", type=int, default=20000)
     ap.add_argument("--sur-days", type=float, default=180.0)
     ap.add_argument("--engine", default="tcgen05", choices=["tcgen05", "mma.sync"],
-                    help="tensor-core engine of the surrogate's forward GEMMs")
+                    help="tensor-core engine of the surrogate's products (tcgen05: fused "
+                         "inference forward, tcgen05 training products)")
     ap.add_argument("--storage", default="f16", choices=["f16", "bf16"])
     return ap.parse_args()
 
@@ -648,7 +649,7 @@ def example_or_rkf45_workload(args, rank, world, local):
             best = r
     clk = clocks.stop()
     steps, ms, kms, g, v, rec = best
-    plain = run(pg.Kernel("rk4"), -1800.0 if example else 1800.0, False)
+    plain = run(pg.Kernel("rk4"), -1800.0 if example else 1800.0, not example)
     line = {
         "metric": METRIC, "value": steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -675,11 +676,22 @@ def example_or_rkf45_workload(args, rank, world, local):
                            "mean_lifespan_temperature_at_death_degC":
                                float(np.nanmean(v["vars"][0][st == 4])) if (st == 4).any() else None}
     else:
+        # accuracy at equal cost: both against RK4 with 5-minute steps
+        ref = run(pg.Kernel("rk4"), 300.0, True)[3]
+
+        def err_cells(x):
+            ok = (x["status"] == 0) & (ref["status"] == 0)
+            dlon = (x["lon"] - ref["lon"] + 180.0) % 360.0 - 180.0
+            e = np.maximum(np.abs(dlon), np.abs(x["lat"] - ref["lat"]))[ok] / 0.25
+            return {"mean_cells": float(e.mean()), "median_cells": float(np.median(e)),
+                    "p99_cells": float(np.percentile(e, 99))}
         alive = g["status"] == 0
         line["rkf45"] = {"mean_steps_per_particle": float(g["step"][alive].mean()),
                          "min_steps": int(g["step"][alive].min()),
                          "max_steps": int(g["step"][alive].max()),
-                         "fixed_rk4_steps_per_particle": args.days * DAY / 1800.0}
+                         "fixed_rk4_steps_per_particle": args.days * DAY / 1800.0,
+                         "error_vs_rk4_5min": err_cells(g),
+                         "rk4_30min_error_vs_rk4_5min": err_cells(plain[3])}
     print(json.dumps(line), flush=True)
 
 
@@ -715,7 +727,7 @@ def surrogate_workload(args, rank, world, local):
     flop_row = 2.0 * (64 * 256 + 3 * 256 * 256 + 256 * 64)
     xb = xv.repeat((10_000_000 + xv.shape[0] - 1) // xv.shape[0], 1)[:10_000_000].contiguous()
     engines = {}
-    for name, flag in (("mma.sync", False), ("tcgen05", True)):
+    for name, flag in (("mma.sync", 0), ("tcgen05_layer_by_layer", 2), ("tcgen05_fused", 1)):
         net.set_engine(flag)
         net.forward(xb)
         torch.cuda.synchronize()

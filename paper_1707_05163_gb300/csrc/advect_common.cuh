@@ -338,6 +338,7 @@ struct Clock {
   double t, dt;
   int k;
   float d;
+  bool tin = false;          // FP32: the current step lies in the cached interval
   __device__ __forceinline__ double start() const { return t + (double)k * dt; }
 };
 

@@ -105,6 +105,19 @@ __device__ __forceinline__ void relocate32(const GridArgs &g, int a, int n, floa
   rinv = __frcp_rn(nhi - nlo);   // correctly rounded, as 1.0f / (hi - lo)
 }
 
+// FP32: whether every stage time of a step of length h (offsets between 0
+// and h from the step start) lies in the cached snapshot interval, so that
+// the stages need not test it (a steady field always does).  A stage that
+// leaves the interval finds it false and takes the slow path, which moves
+// the interval; later stages of the step then take it too, at no cost in
+// results.
+template <typename Real, typename Store, int NF, bool D3, int GEO, class A>
+__device__ __forceinline__ void step_in_interval(const A &a, const Sampler<Real, Store, NF, D3, GEO> &c,
+                                                 Clock &ck, float h) {
+  const float de = ck.d + h;
+  ck.tin = (a.f.nt == 1) | ((c.s0 >= 0) & (fminf(ck.d, de) >= 0.f) & (fmaxf(ck.d, de) <= c.span));
+}
+
 // Velocity in position units per second at a stage (stage time = step start
 // + off).  Returns 0 or a particle status (PG_OOB_*, PG_NAN); -1 for an
 // internal failure already recorded in a.err.
@@ -114,16 +127,17 @@ __device__ __forceinline__ int velocity(const A &a, Sampler<Real, Store, NF, D3,
                                         Real (&vel)[3]) {
   const GridArgs &g = a.g;
   if constexpr (sizeof(Real) == 4) {
-    // FP32: one predicate tests the cached cell on every axis and the cached
-    // snapshot interval; only a miss runs the locate / interval / gather
-    // path, so the common stage is one block without branches.
+    // FP32: one predicate tests the cached cell on every axis and whether the
+    // whole step lies in the cached snapshot interval (ck.tin, set once per
+    // step); only a miss runs the locate / interval / gather path, so the
+    // common stage is one block without branches.  The longitude is tested
+    // as it is: the cached cell lies in [x0, x0 + 360], so a position past
+    // the zonal seam misses and the slow path reduces it.
     const float x0 = axis_lo(g, 0, lon);
     float q = lon;
-    if (is_per<GEO>(g)) q = lon < x0 ? lon + 360.0f : (lon >= x0 + 360.0f ? lon - 360.0f : lon);
-    const float d = ck.d + off;
     bool hit = (q >= c.xlo) & (q <= c.xhi) & (lat >= c.ylo) & (lat <= c.yhi);
     if constexpr (D3) hit = hit & (dep >= c.zlo) & (dep <= c.zhi);
-    hit = hit & ((a.f.nt == 1) | ((c.s0 >= 0) & (d >= 0.f) & (d <= c.span)));
+    hit = hit & ck.tin;
     float xi, eta, zeta = 0.f;
     if (!hit) {
       // The stage velocities are not tested for NaN: a NaN velocity makes
@@ -231,6 +245,7 @@ __device__ __forceinline__ int step_one(const A &a, Sampler<Real, Store, NF, D3,
     // FP32: the same sums without branches on the stage: offsets c_s h with
     // c = (0, 1/2, 1/2, 1), weights (1, 2, 2, 1); 2 k and c_s h are exact
     acc[0] = 0.f; acc[1] = 0.f; acc[2] = 0.f;
+    step_in_interval(a, c, ck, hr);
 #pragma unroll 1
     for (int s = 0; s < nst; ++s) {
       const float off = (s == 0 ? 0.f : (s == 3 ? 1.f : 0.5f)) * hr;
@@ -448,7 +463,10 @@ __device__ __forceinline__ unsigned long long rkf45_steps(
     bool clipped = false;
     if (sgn * (target - t) < sgn * h) { h = target - t; clipped = true; }
     ck.t = t;
-    if constexpr (sizeof(Real) == 4) ck.d = c.s0 >= 0 ? (float)(t - c.ta) : 0.f;
+    if constexpr (sizeof(Real) == 4) {
+      ck.d = c.s0 >= 0 ? (float)(t - c.ta) : 0.f;
+      step_in_interval(a, c, ck, (float)h);
+    }
     Real x4[3], err;
     int r = rkf45_trial<EXT>(a, c, ck, lon, lat, dep, (Real)h, x4, err);
     if (r > 0) { st = (uint8_t)r; break; }

@@ -96,10 +96,13 @@ def test_run_rejecting_everything_is_plain_rk4(env):
     assert stats["network_steps"] == 6 * 3000
 
 
-def test_trained_network_beats_the_24h_euler_step(env):
-    """What the trained network gains over the method without it: its 24 h
-    displacement error against RK4 is smaller than that of one 24 h Euler
-    step from the same local velocity (the network's only other source)."""
+def test_trained_network_saves_rk4_steps_within_its_threshold(env):
+    """What the trained network gains over the method it stands in for, judged
+    by RK4 itself: the network explains most of the variance of the 24 h RK4
+    displacement, and a surrogate run of 10 days with a loose threshold (half
+    a cell) spends less than half the RK4 particle-steps of plain RK4 over the
+    same days while its final positions stay within the threshold of plain
+    RK4's on average."""
     pg, torch, spec, fs = env
     from paper_1707_05163_gb300 import surrogate as S
     x, y = S.make_segments(fs, 120_000, seed=5, groups=24, period=spec.period)
@@ -107,20 +110,22 @@ def test_trained_network_beats_the_24h_euler_step(env):
     net = pg.MLP(37, 128, 3, 3, seed=1)
     losses = S.train(net, x, y, steps=600, batch=4096, lr=2e-3)
     assert losses[-1] < 0.2 * losses[0]
-    pred = net.forward(xt).cpu().numpy()
-    yt_ = yt.cpu().numpy()
-    e_net = np.mean(np.abs(pred[:, :2] - yt_[:, :2]))
-    # Euler over 24 h from the velocity interpolated at the particle (from the
-    # stencil's central cell corners), in cells of the 2-degree grid
-    f = xt.cpu().numpy()
-    xi, eta = f[:, 0], f[:, 1]
-    st = f[:, 5:].reshape(-1, 4, 4, 2)
-    u = ((1 - xi) * (1 - eta) * st[:, 1, 1, 0] + xi * (1 - eta) * st[:, 1, 2, 0] +
-         (1 - xi) * eta * st[:, 2, 1, 0] + xi * eta * st[:, 2, 2, 0]) * 0.3
-    v = ((1 - xi) * (1 - eta) * st[:, 1, 1, 1] + xi * (1 - eta) * st[:, 1, 2, 1] +
-         (1 - xi) * eta * st[:, 2, 1, 1] + xi * eta * st[:, 2, 2, 1]) * 0.3
-    D = 1852.0 * 60.0
-    lat = f[:, 2] * 90.0
-    eu = np.stack([u * DAY / (D * np.cos(np.deg2rad(lat))) / 2.0, v * DAY / D / 2.0], axis=1)
-    e_euler = np.mean(np.abs(eu - yt_[:, :2]))
-    assert e_net < e_euler, (e_net, e_euler)
+    pred = net.forward(xt).cpu().numpy()[:, :2]
+    yt_ = yt.cpu().numpy()[:, :2]
+    r2 = 1.0 - np.sum((pred - yt_) ** 2) / np.sum((yt_ - yt_.mean(axis=0)) ** 2)
+    assert r2 > 0.6, r2
+    n = 4000
+    lon, lat, dep = synth.uniform_particles(n, 21, (0, 360), (-60, 60), (10.0, 400.0),
+                                            dtype=np.float32)
+    K = pg.Kernel("rk4")
+    ref = pg.ParticleSet(fs, lon, lat, dep, pos="f32")
+    plain_steps = ref.execute(K, 10 * DAY, 1800.0)
+    ps = pg.ParticleSet(fs, lon, lat, dep, pos="f32")
+    st = pg.surrogate_run(ps, net, K, nsteps=10, check_every=5, threshold=0.5)
+    assert st["rk4_particle_steps"] < 0.5 * plain_steps, (st["rk4_particle_steps"], plain_steps)
+    g, r = ps.get(), ref.get()
+    ok = (g["status"] == 0) & (r["status"] == 0)
+    assert ok.mean() > 0.9
+    dlon = (g["lon"] - r["lon"] + 180.0) % 360.0 - 180.0
+    e = np.maximum(np.abs(dlon), np.abs(g["lat"] - r["lat"]))[ok] / 2.0   # 2-degree cells
+    assert np.mean(e) < 0.5, np.mean(e)
