@@ -53,15 +53,19 @@ def parse():
     ap.add_argument("--e2e-ring", type=int, default=4,
                     help="snapshot ring slots of the end-to-end leg (4: two in use + the next)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-mlp", action="store_true",
+                    help="skip the surrogate network's inference timing in the 3-D line")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="3d",
-                    choices=["3d", "precision", "batch", "surrogate", "example", "rkf45"],
+                    choices=["3d", "precision", "batch", "surrogate", "example", "rkf45", "mlp"],
                     help="3d: the FP32 3-D workload (default); precision: 2-D 1/12 deg "
                          "cell-index + FP16/BF16 form against plain FP32; batch: 256 "
                          "releases in one persistent launch per day, graph-captured; "
                          "example: the worked example's backward two-phase run with "
                          "sampled temperature and daily indexed output; rkf45: adaptive "
-                         "RKF45 on the 3-D workload")
+                         "RKF45 on the 3-D workload; mlp: the surrogate network's "
+                         "inference on --mlp-rows feature rows, three engines")
+    ap.add_argument("--mlp-rows", type=int, default=10_000_000)
     ap.add_argument("--rkf45-tol", type=float, default=10.0, help="metres per step")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="shrink every release of the batch workload (tests)")
@@ -188,6 +192,48 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def bf16_burst_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def mlp_forward_leg(pg, torch, dev, x=None, rows=10_000_000, engines=(("tcgen05_fused", 1),),
+                    net=None, reps=5):
+    """Inference throughput of the surrogate network (37 inputs padded to 64,
+    4 hidden layers of 256, 3 outputs padded to 64: 2 * (64*256 + 3*256*256 +
+    256*64) FLOP per row) on `rows` feature rows resident on the device, input
+    packing included; CUDA events on the current stream, best of `reps`, one
+    warm-up.  Random-initialised weights unless a trained `net` is given."""
+    flop_row = 2.0 * (64 * 256 + 3 * 256 * 256 + 256 * 64)
+    if net is None:
+        net = pg.MLP(37, 256, 4, 3, seed=5)
+    if x is None:
+        g = torch.Generator(device=dev)
+        g.manual_seed(7)
+        x = torch.randn(rows, 37, device=dev, generator=g)
+    peak, kind = bf16_burst_peak()
+    out = {}
+    for name, flag in engines:
+        net.set_engine(flag)
+        net.forward(x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = float("inf")
+        for _ in range(reps):
+            e0.record()
+            net.forward(x)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        tf = flop_row * x.shape[0] / (best * 1e-3) / 1e12
+        out[name] = {"ms_per_10M_rows": best * 1e7 / x.shape[0], "TFLOPs": tf,
+                     "frac_of_bf16_peak": tf / peak, "peak_TFLOPs": peak, "peak_source": kind}
+    return out
+
+
 def make_field_host_bases(gf):
     return [gf.base2d(s) for s in range(len(gf.times))]
 
@@ -248,6 +294,8 @@ def main():
         return surrogate_workload(args, rank, world, local)
     if args.workload in ("example", "rkf45"):
         return example_or_rkf45_workload(args, rank, world, local)
+    if args.workload == "mlp":
+        return mlp_workload(args, rank, world, local)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -365,6 +413,12 @@ def main():
                     "peak_GBps": hbm_peak, "frac": b * kernel_rate / 1e9 / hbm_peak,
                     "peak_source": peak_kind}
     gather_gbs = ALGO_BYTES_PER_STEP * kernel_rate / 1e9
+    mlp = None
+    if rank == 0 and not args.no_mlp:
+        mlp = mlp_forward_leg(pg, torch, dev)["tcgen05_fused"]
+        mlp["rows"] = 10_000_000
+        mlp["network"] = ("surrogate MLP 37-256x4-3, random-initialised BF16 weights, fused "
+                          "tcgen05 inference kernel (input packing included)")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
@@ -385,7 +439,7 @@ def main():
                      "kernel": "advect_plain_kernel<float, float, 3, true, GEO_SPH_PER>",
                      "algorithmic_flops_per_particle_step": ALGO_FLOPS_PER_STEP,
                      "avg_launch_ms": avg_launch_s * 1e3, "launches": kern_launches,
-                     "l2": l2_view, "hbm": hbm_view,
+                     "l2": l2_view, "hbm": hbm_view, "l2_read_peak_GBps": l2_peak,
                      "traffic_capture": cap.get("captured") if cap else None,
                      "gather_view": {"algorithmic_bytes_per_particle_step": ALGO_BYTES_PER_STEP,
                                      "effective_GBps": gather_gbs,
@@ -398,6 +452,7 @@ def main():
         "e2e": e2e,
         "streamed": streamed,
         "output": output,
+        "surrogate_mlp_forward": mlp,
         "gpu_launches": int(c1.value - c0.value),
         "clocks": clk,
         "particle_steps": total_all,
@@ -695,6 +750,45 @@ def example_or_rkf45_workload(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def mlp_workload(args, rank, world, local):
+    """The surrogate network alone (37 inputs, 4 hidden layers of 256, 3
+    outputs; random-initialised BF16 weights): inference on --mlp-rows
+    Gaussian feature rows resident on the device, for the fused tcgen05
+    kernel, the layer-by-layer tcgen05 products and the mma.sync products.
+    `value` is the fused kernel's rows per second; one process, replicas
+    only (the rows are independent)."""
+    import ctypes as C
+    import torch
+    import paper_1707_05163_gb300 as pg
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = pg.load()
+    c0, c1 = C.c_int64(), C.c_int64()
+    lib.pg_launch_count(C.byref(c0))
+    engines = mlp_forward_leg(pg, torch, dev, rows=args.mlp_rows, reps=max(args.steps, 1),
+                              engines=(("tcgen05_fused", 1), ("tcgen05_layer_by_layer", 2),
+                                       ("mma.sync", 0)))
+    lib.pg_launch_count(C.byref(c1))
+    launches = int(c1.value - c0.value)
+    f = engines["tcgen05_fused"]
+    rows_per_s = 1e7 / (f["ms_per_10M_rows"] * 1e-3)
+    line = {
+        "metric": "surrogate MLP inference rows/s", "value": rows_per_s, "unit": "rows/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)",
+        "data": "synthetic (Gaussian feature rows, random-initialised weights)",
+        "config": {"workload": f"surrogate MLP 37-256x4-3 inference, {args.mlp_rows} rows",
+                   "l2": "inputs larger than L2 (1.48 GB of features at 10M rows)"},
+        "roofline": {"bound": "tensor", "achieved": f["TFLOPs"], "peak": f["peak_TFLOPs"],
+                     "unit": "TFLOP/s", "frac": f["frac_of_bf16_peak"], "traffic": None,
+                     "kernel": "mlp_fused_kernel",
+                     "algorithmic_flops_per_row": 2.0 * (64 * 256 + 3 * 256 * 256 + 256 * 64),
+                     "peak_source": f["peak_source"] + " bf16 burst"},
+        "engines": engines, "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def surrogate_workload(args, rank, world, local):
     """Learned-surrogate form: an MLP (37 inputs incl. a 4x4x2 U/V stencil, 4
     hidden layers of 256, GELU, BF16 weights, FP32 accumulation) trained with
@@ -724,19 +818,10 @@ def surrogate_workload(args, rank, world, local):
     del x, y
     # forward throughput of the two tensor-core engines on 10M feature rows
     # (padded network: 2 * (64*256 + 3*256*256 + 256*64) FLOP per row)
-    flop_row = 2.0 * (64 * 256 + 3 * 256 * 256 + 256 * 64)
     xb = xv.repeat((10_000_000 + xv.shape[0] - 1) // xv.shape[0], 1)[:10_000_000].contiguous()
-    engines = {}
-    for name, flag in (("mma.sync", 0), ("tcgen05_layer_by_layer", 2), ("tcgen05_fused", 1)):
-        net.set_engine(flag)
-        net.forward(xb)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(3):
-            net.forward(xb)
-        torch.cuda.synchronize()
-        ms = (time.perf_counter() - t0) / 3 * 1e3
-        engines[name] = {"ms_per_10M_rows": ms, "TFLOPs": flop_row * 1e7 / (ms * 1e-3) / 1e12}
+    engines = mlp_forward_leg(pg, torch, dev, x=xb, net=net,
+                              engines=(("mma.sync", 0), ("tcgen05_layer_by_layer", 2),
+                                       ("tcgen05_fused", 1)))
     del xb
     net.set_engine(args.engine == "tcgen05")
     pred = net.forward(xv)

@@ -398,7 +398,12 @@ PG_API pg_status pg_mlp_num_params(const pg_mlp *net, int64_t *padded, int64_t *
  * [dout x din] row-major then b_l [dout]; din/dout are the padded widths. */
 PG_API pg_status pg_mlp_get_params(const pg_mlp *net, float *host);
 PG_API pg_status pg_mlp_set_params(pg_mlp *net, const float *host);
-/* Forward products on tcgen05 (1) or warp-level mma.sync (0, default). */
+/* Engine of the products: 0 warp-level mma.sync (default); 1 tcgen05 (5th-
+ * generation tensor cores, accumulators in tensor memory): every product
+ * whose widths are 64 or 256, and for the surrogate's shape (input and
+ * output padded to 64, four hidden layers of 256) inference as one fused
+ * kernel that keeps the activations on chip; 2 tcgen05 products without the
+ * fused inference (layer by layer, for comparison). */
 PG_API pg_status pg_mlp_set_engine(pg_mlp *net, int tcgen05);
 /* y [M x n_out] = net(x [M x n_in]); device FP32 arrays, on `stream`. */
 PG_API pg_status pg_mlp_forward(pg_mlp *net, const float *x, int64_t M, float *y, void *stream);

@@ -469,7 +469,9 @@ class MLP:
         N.check(self._lib.pg_mlp_set_params(self.h, flat.ctypes.data))
 
     def set_engine(self, tcgen05):
-        N.check(self._lib.pg_mlp_set_engine(self.h, int(bool(tcgen05))))
+        """0/False: mma.sync; 1/True: tcgen05 (fused inference where the shape
+        allows); 2: tcgen05 layer by layer."""
+        N.check(self._lib.pg_mlp_set_engine(self.h, int(tcgen05)))
 
     def forward(self, x, out=None, stream=None):
         """x: CUDA float32 tensor [M x n_in] -> CUDA float32 tensor [M x n_out]."""

@@ -31,6 +31,7 @@ UNITS = {
     "batch.cu": [],
     "mlp.cu": [],
     "mlp_tc.cu": [],
+    "mlp_fused.cu": [],
     "surrogate.cu": [],
     "advect_f32.cu": ([f"-maxrregcount={os.environ['PG_MAXRREG']}"]
                       if os.environ.get("PG_MAXRREG") else []),

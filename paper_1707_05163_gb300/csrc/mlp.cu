@@ -70,15 +70,18 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 }  // namespace
 
 // GELU in its tanh form, 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))),
-// with the hardware tanh approximation (relative error below 2^-10).
+// with the hardware tanh approximation (relative error below 2^-10); the
+// forward writes it as h + h t with h = x / 2 and the tanh argument
+// x (c0 + c1 x^2), the expression of the tcgen05 kernels.
 __device__ __forceinline__ float tanh_fast(float x) {
   float y;
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 __device__ __forceinline__ float gelu(float x) {
-  const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
-  return 0.5f * x * (1.0f + tanh_fast(u));
+  const float p = fmaf(x * x, 0.035677408136300125f, 0.7978845608028654f);
+  const float h = 0.5f * x;
+  return fmaf(h, tanh_fast(x * p), h);
 }
 __device__ __forceinline__ float gelu_grad(float x) {
   const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
@@ -360,7 +363,10 @@ struct pg_mlp {
   float *gscratch = nullptr;          // split-K partials of the weight gradient
   size_t gscratch_bytes = 0;
   float *loss_partial = nullptr;
-  int use_tc = 0;                     // tcgen05 forward when available
+  int use_tc = 0;                     // tcgen05 products when available
+  int fused = 1;                      // tcgen05 inference in one fused kernel when the shape allows
+  uint8_t *wpk = nullptr;             // weights packed for the fused forward
+  bool wpk_valid = false;
   int *d_err = nullptr;               // device word: tcgen05 wait gave up
 };
 
@@ -369,6 +375,11 @@ cudaError_t gemm_nt_tc(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, 
                        int64_t M, int N, int K, const float *bias, int act, float *out_f32,
                        __nv_bfloat16 *out_bf16, __nv_bfloat16 *pre_bf16, int ldc, cudaStream_t st,
                        int *err, const __nv_bfloat16 *gin = nullptr);
+size_t mlp_fused_packed_bytes();
+cudaError_t mlp_fused_pack(const __nv_bfloat16 *const w[5], uint8_t *out, cudaStream_t st);
+cudaError_t mlp_fused_forward(const float *x, int64_t M, int n_in, const uint8_t *wpk,
+                              const float *const bias[5], float *y, int n_out, cudaStream_t st,
+                              int *err);
 cudaError_t gemm_tn_splitk_tc(const __nv_bfloat16 *A, int64_t lda, int Mrows,
                               const __nv_bfloat16 *B, int64_t ldb, int N, int64_t K, float *out,
                               float *scratch, size_t scratch_bytes, cudaStream_t st, int *err);
@@ -428,6 +439,7 @@ cudaError_t ensure_ws(pg_mlp *n, int64_t rows) {
 
 // BF16 copies of the weights and of their transposes from the FP32 masters
 cudaError_t refresh_bf16(pg_mlp *n, cudaStream_t st) {
+  n->wpk_valid = false;
   f32_to_bf16<<<grid1((int64_t)n->nparam), 256, 0, st>>>(n->w, (int64_t)n->nparam, n->wb);
   note_launches(1);
   for (int l = 0; l < n->nl; ++l) {
@@ -577,6 +589,7 @@ pg_status pg_mlp_create(int n_in, int width, int depth, int n_out, uint64_t seed
   if (e == cudaSuccess) e = dev_alloc((void **)&n->wbt, off * 2);
   if (e == cudaSuccess) e = dev_alloc((void **)&n->d_err, 4);
   if (e == cudaSuccess) e = cudaMemset(n->d_err, 0, 4);
+  if (e == cudaSuccess) e = dev_alloc((void **)&n->wpk, mlp_fused_packed_bytes());
   if (e == cudaSuccess) e = cudaMemcpy(n->w, h.data(), off * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(n->m, 0, off * 4);
   if (e == cudaSuccess) e = cudaMemset(n->v, 0, off * 4);
@@ -603,6 +616,7 @@ pg_status pg_mlp_destroy(pg_mlp *n) {
   dev_free(n->w); dev_free(n->m); dev_free(n->v); dev_free(n->g); dev_free(n->wb);
   dev_free(n->wbt);
   dev_free(n->d_err);
+  dev_free(n->wpk);
   delete n;
   return PG_OK;
 }
@@ -642,8 +656,9 @@ pg_status pg_mlp_set_params(pg_mlp *n, const float *host) {
 
 pg_status pg_mlp_set_engine(pg_mlp *n, int tcgen05) {
   clear_error();
-  if (!n) { set_error("invalid argument"); return PG_ERR_ARG; }
+  if (!n || tcgen05 < 0 || tcgen05 > 2) { set_error("invalid argument"); return PG_ERR_ARG; }
   n->use_tc = tcgen05 ? 1 : 0;
+  n->fused = tcgen05 == 1 ? 1 : 0;
   return PG_OK;
 }
 
@@ -653,7 +668,23 @@ pg_status pg_mlp_forward(pg_mlp *n, const float *x, int64_t M, float *y, void *s
   if (!n || (M > 0 && (!x || !y)) || M < 0) { set_error("invalid argument"); return PG_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t chunk = 1 << 20;
-  for (int64_t r0 = 0; r0 < M; r0 += chunk) {
+  // the surrogate's shape runs as one fused tcgen05 kernel (activations on chip)
+  const bool fused = n->use_tc && n->fused && n->pin == 64 && n->width == 256 && n->depth == 4 &&
+                     n->pout == 64 && n->n_out <= 16;
+  if (fused && !n->wpk_valid) {
+    const __nv_bfloat16 *w[5];
+    for (int l = 0; l < 5; ++l) w[l] = n->wb + n->woff[l];
+    CUM(mlp_fused_pack(w, n->wpk, st));
+    n->wpk_valid = true;
+  }
+  if (fused) {
+    // one launch over all rows: the kernel reads the FP32 features itself
+    // and needs no workspace
+    const float *bias[5];
+    for (int l = 0; l < 5; ++l) bias[l] = n->w + n->boff[l];
+    CUM(mlp_fused_forward(x, M, n->n_in, n->wpk, bias, y, n->n_out, st, n->d_err));
+  }
+  for (int64_t r0 = 0; r0 < M && !fused; r0 += chunk) {
     const int64_t rows = std::min(chunk, M - r0);
     CUM(ensure_ws(n, std::min<int64_t>(M, chunk)));
     pack_input<<<grid1(rows * n->pin), 256, 0, st>>>(x + r0 * n->n_in, rows, n->n_in, n->pin, n->x0);

@@ -37,12 +37,16 @@ __device__ __forceinline__ uint32_t su32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// GELU in its tanh form (as in mlp.cu), hardware tanh approximation.
+// GELU in its tanh form, 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))),
+// written as h + h t with h = x / 2 and the tanh argument x (c0 + c1 x^2);
+// hardware tanh approximation.  The same expression as mlp.cu and the fused
+// forward (mlp_fused.cu).
 __device__ __forceinline__ float gelu_tc(float x) {
-  const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
+  const float p = fmaf(x * x, 0.035677408136300125f, 0.7978845608028654f);
   float t;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
-  return 0.5f * x * (1.0f + t);
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(x * p));
+  const float h = 0.5f * x;
+  return fmaf(h, t, h);
 }
 
 // Its derivative, as mlp.cu's gelu_grad.

@@ -95,16 +95,19 @@ def _close(a, b, rel=3e-2):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("engine", ["mma.sync", "tcgen05"])
+@pytest.mark.parametrize("engine", ["mma.sync", "tcgen05", "tcgen05_layers"])
 @pytest.mark.parametrize("shape", [(37, 256, 4, 3), (5, 64, 2, 3), (70, 128, 3, 40)])
 def test_forward_and_gradient_against_oracle(gpu, shape, engine):
-    """Both tensor-core engines against the FP64 oracle (the tcgen05 engine
-    runs the products whose widths are 64 or 256; other widths, as in the
-    third shape, take the mma.sync products)."""
+    """The tensor-core engines against the FP64 oracle: mma.sync; tcgen05,
+    whose forward on the surrogate's shape (the first) is the fused
+    inference kernel; tcgen05 layer by layer.  The tcgen05 engines run the
+    products whose widths are 64 or 256; other widths, as in the third
+    shape, take the mma.sync products.  Gradients always run layer by
+    layer."""
     pg, torch = gpu
     n_in, width, depth, n_out = shape
     net = pg.MLP(n_in, width, depth, n_out, seed=7)
-    net.set_engine(engine == "tcgen05")
+    net.set_engine({"mma.sync": 0, "tcgen05": 1, "tcgen05_layers": 2}[engine])
     o = MLPOracle(n_in, width, depth, n_out)
     rng = np.random.default_rng(1)
     p = _random_params(o, rng).astype(np.float32)
@@ -161,3 +164,29 @@ def test_tcgen05_forward_matches_mma_sync(gpu, M):
     y2 = net.forward(x).cpu().numpy()
     np.testing.assert_array_equal(y1, y2)
     _close(y1, y0, rel=1e-2)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("M", [1, 100, 128, 129, 40_000, 300_001])
+def test_fused_tcgen05_forward_equals_layer_by_layer(gpu, M):
+    """The fused inference kernel (activations kept on chip, weights streamed
+    in pieces) issues the same tcgen05 products in the same order and applies
+    the same epilogue as the layer-by-layer tcgen05 forward, so the outputs
+    are identical; ragged row counts and several tiles per CTA."""
+    pg, torch = gpu
+    net = pg.MLP(37, 256, 4, 3, seed=13)
+    rng = np.random.default_rng(M)
+    x = torch.from_numpy(rng.normal(size=(M, 37)).astype(np.float32)).cuda()
+    net.set_engine(2)                  # tcgen05, layer by layer
+    y_layers = net.forward(x).cpu().numpy()
+    net.set_engine(1)                  # tcgen05, fused
+    y_fused = net.forward(x).cpu().numpy()
+    np.testing.assert_array_equal(y_fused, y_layers)
+    # after a training step the packed weights follow the new parameters
+    t = torch.from_numpy(rng.normal(size=(4096, 3)).astype(np.float32)).cuda()
+    xs = torch.from_numpy(rng.normal(size=(4096, 37)).astype(np.float32)).cuda()
+    net.train_step(xs, t, 1e-3)
+    y2 = net.forward(x).cpu().numpy()
+    net.set_engine(2)
+    np.testing.assert_array_equal(y2, net.forward(x).cpu().numpy())
+    assert not np.array_equal(y2, y_fused)
