@@ -848,7 +848,7 @@ def surrogate_workload(args, rank, world, local):
     runs = {}
     for thr in (1e-3, 1e-2, 1e-1):
         ps = pg.ParticleSet(fs, dl, da, dd, pos="f32")
-        ps.set_tune(args.block, 0, 48)
+        ps.set_tune(args.block, args.resort_steps, 48)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st = pg.surrogate_run(ps, net, K, nsteps=nsteps, check_every=5, threshold=thr)

@@ -448,8 +448,11 @@ typedef struct {
  * steps of dt_check from the same state: particles whose position differs by
  * more than `threshold` cells (depth: layers), and particles that the network
  * or the checking RK4 deleted within the block, are re-integrated with RK4
- * from the start of the block; all others take RK4's state for the checked
- * step.  The kernel `k` is the checking RK4's. */
+ * from the start of the block (packed into a dense set, then written back);
+ * all others take RK4's state for the checked step.  The kernel `k` is the
+ * checking RK4's.  If the set's tuning has re-sorts (resort_steps > 0), the
+ * particles are put in Morton order at the start of every block (their
+ * storage order changes; ids are kept). */
 PG_API pg_status pg_surrogate_run(pg_pset *ps, pg_mlp *net, const pg_kernel *k, int nsteps,
                                   int check_every, double horizon, double dt_check,
                                   double threshold, pg_surrogate_stats *stats, void *stream);

@@ -195,6 +195,17 @@ cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t m, uint32_
 
 }  // namespace
 
+// Exclusive scan of m 32-bit entries (m at most scan_max_entries()) with a
+// scratch of scan_scratch_words(m) words; in may equal out.
+int64_t scan_max_entries() { return (int64_t)kScanTile * kScanTile; }
+size_t scan_scratch_words(int64_t m) { return (size_t)(2 * ((m + kScanTile - 1) / kScanTile) + 1); }
+cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t m, uint32_t *tmp,
+                               cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  if (m > scan_max_entries()) return cudaErrorInvalidValue;
+  return exclusive_scan(in, out, m, tmp, st);
+}
+
 // n_alive == nullptr: keep the particle arrays where they are (the sorted
 // copy is copied back) and read nothing back to the host, so the whole
 // re-sort is a fixed sequence of device operations (capturable in a graph).

@@ -53,17 +53,17 @@ __global__ void features_kernel(GridArgs g, FieldArgs f, const float *lon, const
       i = g.nx - 1;
       xi = (q - g.lonf[g.nx - 1]) / (g.lon_end_f - g.lonf[g.nx - 1]);
     } else {
-      i = find_cell(g.lonf, g.nx, q);
+      i = axis_search<float>(g, 0, g.nx, q);
       xi = (q - g.lonf[i]) / (g.lonf[i + 1] - g.lonf[i]);
     }
     const float y = fminf(fmaxf(lat[p], g.latf[0]), g.latf[g.ny - 1]);
-    const int j = find_cell(g.latf, g.ny, y);
+    const int j = axis_search<float>(g, 1, g.ny, y);
     const float eta = (y - g.latf[j]) / (g.latf[j + 1] - g.latf[j]);
     int k = 0;
     float zeta = 0.f;
     if (g.nz > 1) {
       const float z = fminf(fmaxf(dep[p], g.depthf[0]), g.depthf[g.nz - 1]);
-      k = find_cell(g.depthf, g.nz, z);
+      k = axis_search<float>(g, 2, g.nz, z);
       zeta = (z - g.depthf[k]) / (g.depthf[k + 1] - g.depthf[k]);
     }
     // time interval
@@ -95,16 +95,18 @@ __global__ void features_kernel(GridArgs g, FieldArgs f, const float *lon, const
         int ii = i + di;
         if (ii < 0) ii += g.nx;
         if (ii >= g.nx) ii -= g.nx;
-        float uv[2];
-        for (int c = 0; c < 2; ++c) {
-          const size_t n0 = (((size_t)k * g.ny + jj) * g.nx + ii) * stride + c;
-          const size_t n1 = g.nz > 1 ? n0 + (size_t)g.ny * g.nx * stride : n0;
-          const float a = S0[n0] + (S0[n1] - S0[n0]) * zeta;
-          const float b = S1[n0] + (S1[n1] - S1[n0]) * zeta;
-          uv[c] = (a + (b - a) * tau) * kVelScale;
-        }
-        o[q2++] = uv[0];
-        o[q2++] = uv[1];
+        // U and V of a node are adjacent in the slab: one 8-byte load per
+        // node, level and snapshot
+        const size_t n0 = (((size_t)k * g.ny + jj) * g.nx + ii) * stride;
+        const size_t n1 = g.nz > 1 ? n0 + (size_t)g.ny * g.nx * stride : n0;
+        const float2 a0 = __ldg(reinterpret_cast<const float2 *>(S0 + n0));
+        const float2 a1 = __ldg(reinterpret_cast<const float2 *>(S0 + n1));
+        const float2 b0 = __ldg(reinterpret_cast<const float2 *>(S1 + n0));
+        const float2 b1 = __ldg(reinterpret_cast<const float2 *>(S1 + n1));
+        const float au = a0.x + (a1.x - a0.x) * zeta, bu = b0.x + (b1.x - b0.x) * zeta;
+        const float av = a0.y + (a1.y - a0.y) * zeta, bv = b0.y + (b1.y - b0.y) * zeta;
+        o[q2++] = (au + (bu - au) * tau) * kVelScale;
+        o[q2++] = (av + (bv - av) * tau) * kVelScale;
       }
     }
   }
@@ -193,25 +195,53 @@ __global__ void check_kernel(GridArgs g, const float *lon_a, const float *lat_a,
   atomicAdd(n_reject, r_acc);
 }
 
-// Accepted particles are parked (status 255, skipped by the advection
-// kernels) while the rejected ones, restored from the checkpoint, are
-// re-integrated; unpark turns 255 back into alive.
-__global__ void park_kernel(uint8_t *status, const uint8_t *reject, int64_t n) {
+// The rejected particles are re-integrated as a dense set: their
+// checkpoint states are packed, in particle order, into the arrays of a
+// second set (position k of the rejected ones given by an exclusive scan of
+// the reject flags), advanced there, and written back to their places.
+__global__ void flags_kernel(const uint8_t *reject, int64_t n, uint32_t *flags) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x)
-    if (!reject[p] && status[p] == 0) status[p] = 255;
+    flags[p] = reject[p] ? 1u : 0u;
 }
-__global__ void unpark_kernel(uint8_t *status, int64_t n) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x)
-    if (status[p] == 255) status[p] = 0;
+
+struct SetPtrs {
+  float *x, *y, *z;
+  double *time;
+  uint64_t *id;
+  uint32_t *step;
+  uint8_t *status;
+};
+
+// Particles p0 .. p0 + n - 1; offs is the exclusive scan of their flags and
+// base the number of rejected particles before p0.
+__global__ void pack_rejected_kernel(const uint8_t *reject, const uint32_t *offs, int64_t p0,
+                                     int64_t n, uint32_t base, SetPtrs src, SetPtrs dst,
+                                     uint32_t *idx) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = p0 + i;
+    if (!reject[p]) continue;
+    const uint32_t k = base + offs[i];
+    idx[k] = (uint32_t)p;
+    dst.x[k] = src.x[p]; dst.y[k] = src.y[p]; dst.z[k] = src.z[p];
+    dst.time[k] = src.time[p]; dst.id[k] = src.id[p]; dst.step[k] = src.step[p];
+    dst.status[k] = src.status[p];
+  }
 }
-// rejected particles take the checkpoint state
-template <typename T>
-__global__ void select_kernel(T *dst, const T *ckpt, const uint8_t *reject, int64_t n) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x)
-    if (reject[p]) dst[p] = ckpt[p];
+
+__global__ void unpack_rejected_kernel(const uint32_t *idx, int64_t m, SetPtrs src, SetPtrs dst) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t p = idx[k];
+    dst.x[p] = src.x[k]; dst.y[p] = src.y[k]; dst.z[p] = src.z[k];
+    dst.time[p] = src.time[k]; dst.step[p] = src.step[k]; dst.status[p] = src.status[k];
+  }
+}
+
+SetPtrs set_ptrs(pg_pset *ps) {
+  return SetPtrs{(float *)ps->x, (float *)ps->y, (float *)ps->z, ps->time, ps->id, ps->step,
+                 ps->status};
 }
 
 int grid_of(int64_t n, int sm) {
@@ -229,6 +259,12 @@ FieldArgs field_args(const pg_fieldset *fs) {
 }
 
 }  // namespace
+
+cudaError_t launch_resort(pg_pset *ps, cudaStream_t st, int64_t *n_alive);
+int64_t scan_max_entries();
+size_t scan_scratch_words(int64_t m);
+cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t m, uint32_t *tmp,
+                               cudaStream_t st);
 
 }  // namespace pg
 
@@ -342,15 +378,18 @@ pg_status pg_surrogate_run(pg_pset *ps, pg_mlp *net, const pg_kernel *k, int nst
   uint8_t *rej = nullptr;
   double *esum = nullptr;
   unsigned long long *nrej = nullptr;
-  pg_pset *ckpt = nullptr, *chk = nullptr;
+  uint32_t *flags = nullptr, *offs = nullptr, *scan_tmp = nullptr, *idx = nullptr;
+  pg_pset *ckpt = nullptr, *chk = nullptr, *rset = nullptr;
   cudaEvent_t e0, e1, e2;
   CUS(cudaEventCreate(&e0));
   CUS(cudaEventCreate(&e1));
   CUS(cudaEventCreate(&e2));
   auto cleanup = [&]() {
     dev_free(x); dev_free(y); dev_free(rej); dev_free(esum); dev_free(nrej);
+    dev_free(flags); dev_free(offs); dev_free(scan_tmp); dev_free(idx);
     if (ckpt) pg_pset_destroy(ckpt);
     if (chk) pg_pset_destroy(chk);
+    if (rset) pg_pset_destroy(rset);
     cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
   };
   cudaError_t e = dev_alloc((void **)&x, (size_t)std::max<int64_t>(n, 1) * kFeat * 4);
@@ -358,6 +397,12 @@ pg_status pg_surrogate_run(pg_pset *ps, pg_mlp *net, const pg_kernel *k, int nst
   if (e == cudaSuccess) e = dev_alloc((void **)&rej, (size_t)std::max<int64_t>(n, 1));
   if (e == cudaSuccess) e = dev_alloc((void **)&esum, 16);
   if (e == cudaSuccess) e = dev_alloc((void **)&nrej, 8);
+  // compaction of the rejected particles, in pieces of at most one scan
+  const int64_t piece = std::min<int64_t>(std::max<int64_t>(n, 1), scan_max_entries());
+  if (e == cudaSuccess) e = dev_alloc((void **)&flags, (size_t)piece * 4);
+  if (e == cudaSuccess) e = dev_alloc((void **)&offs, (size_t)piece * 4);
+  if (e == cudaSuccess) e = dev_alloc((void **)&scan_tmp, scan_scratch_words(piece) * 4);
+  if (e == cudaSuccess) e = dev_alloc((void **)&idx, (size_t)std::max<int64_t>(n, 1) * 4);
   if (e != cudaSuccess) {
     cleanup();
     set_error("surrogate buffers: %s", cudaGetErrorString(e));
@@ -368,7 +413,9 @@ pg_status pg_surrogate_run(pg_pset *ps, pg_mlp *net, const pg_kernel *k, int nst
   if ((r = pg_pset_create(ps->fs, 0, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr, 0,
                           PG_POS_F32, ps->seed, &ckpt)) ||
       (r = pg_pset_create(ps->fs, 0, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr, 0,
-                          PG_POS_F32, ps->seed, &chk))) {
+                          PG_POS_F32, ps->seed, &chk)) ||
+      (r = pg_pset_create(ps->fs, 0, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr, 0,
+                          PG_POS_F32, ps->seed, &rset))) {
     cleanup();
     return r;
   }
@@ -406,6 +453,13 @@ pg_status pg_surrogate_run(pg_pset *ps, pg_mlp *net, const pg_kernel *k, int nst
   int done_steps = 0;
   while (done_steps < nsteps && r == PG_OK) {
     const int blk = std::min(check_every, nsteps - done_steps);
+    // Morton order at the start of every block (when the set's tuning asks
+    // for re-sorts), for the locality of the features, checks and fallback
+    if (ps->tune.resort_steps > 0 && n > 0) {
+      int64_t alive = 0;
+      e = launch_resort(ps, st, &alive);
+      if (e) { r = PG_ERR_CUDA; set_error("re-sort: %s", cudaGetErrorString(e)); break; }
+    }
     e = copy_set(ckpt, ps);
     if (e) { r = PG_ERR_CUDA; set_error("checkpoint copy: %s", cudaGetErrorString(e)); break; }
     cudaEventRecord(e0, st);
@@ -437,29 +491,48 @@ pg_status pg_surrogate_run(pg_pset *ps, pg_mlp *net, const pg_kernel *k, int nst
     S.rejected += (int64_t)h_nrej;
     // everyone takes RK4's state for the checked step ...
     if ((e = copy_set(ps, chk))) { r = PG_ERR_CUDA; set_error("%s", cudaGetErrorString(e)); break; }
-    // ... and the rejected re-integrate the whole block from the checkpoint
+    // ... and the rejected re-integrate the whole block from the checkpoint,
+    // packed into a dense set
     if (h_nrej > 0) {
-      const int g = grid_of(n, sm);
-      select_kernel<float><<<g, 256, 0, st>>>((float *)ps->x, (const float *)ckpt->x, rej, n);
-      select_kernel<float><<<g, 256, 0, st>>>((float *)ps->y, (const float *)ckpt->y, rej, n);
-      select_kernel<float><<<g, 256, 0, st>>>((float *)ps->z, (const float *)ckpt->z, rej, n);
-      select_kernel<double><<<g, 256, 0, st>>>(ps->time, ckpt->time, rej, n);
-      select_kernel<uint32_t><<<g, 256, 0, st>>>(ps->step, ckpt->step, rej, n);
-      select_kernel<uint8_t><<<g, 256, 0, st>>>(ps->status, ckpt->status, rej, n);
-      park_kernel<<<g, 256, 0, st>>>(ps->status, rej, n);
-      note_launches(7);
-      const pg_tune saved = ps->tune;
-      ps->tune = keep_order;
-      const double tmin = ps->t_min, tmax = ps->t_max;
-      ps->t_min = ckpt->t_min;
-      ps->t_max = ckpt->t_max;
-      r = pg_execute(ps, k, blk * horizon, dt_check, 0.0, nullptr, nullptr, st, &rk);
-      ps->tune = saved;
-      ps->t_min = tmin;
-      ps->t_max = tmax;
-      unpark_kernel<<<g, 256, 0, st>>>(ps->status, n);
+      const int64_t m = (int64_t)h_nrej;
+      if (rset->cap < m) {
+        PsetArrays A;
+        if (alloc_arrays(A, PG_POS_F32, m, rset->nvar) != PG_OK) {
+          r = PG_ERR_NOMEM;
+          set_error("surrogate fallback set of %lld particles", (long long)m);
+          break;
+        }
+        pset_arrays(rset).free_all();
+        pset_set_arrays(rset, A);
+        rset->cap = m;
+      }
+      const SetPtrs cp = set_ptrs(ckpt), rp = set_ptrs(rset), pp = set_ptrs(ps);
+      uint32_t base = 0;
+      for (int64_t p0 = 0; p0 < n && !e; p0 += piece) {
+        const int64_t len = std::min(piece, n - p0);
+        const int g = grid_of(len, sm);
+        flags_kernel<<<g, 256, 0, st>>>(rej + p0, len, flags);
+        e = exclusive_scan_u32(flags, offs, len, scan_tmp, st);
+        if (e) break;
+        pack_rejected_kernel<<<g, 256, 0, st>>>(rej, offs, p0, len, base, cp, rp, idx);
+        note_launches(2);
+        if (p0 + len < n) {
+          // the next piece's rejected particles follow this piece's
+          uint32_t last_off = 0, last_flag = 0;
+          e = cudaMemcpyAsync(&last_off, offs + len - 1, 4, cudaMemcpyDeviceToHost, st);
+          if (!e) e = cudaMemcpyAsync(&last_flag, flags + len - 1, 4, cudaMemcpyDeviceToHost, st);
+          if (!e) e = cudaStreamSynchronize(st);
+          base += last_off + last_flag;
+        }
+      }
+      if (e) { r = PG_ERR_CUDA; set_error("fallback packing: %s", cudaGetErrorString(e)); break; }
+      rset->n = m;
+      rset->t_min = ckpt->t_min;
+      rset->t_max = ckpt->t_max;
+      rset->tune = keep_order;
+      if ((r = pg_execute(rset, k, blk * horizon, dt_check, 0.0, nullptr, nullptr, st, &rk))) break;
+      unpack_rejected_kernel<<<grid_of(m, sm), 256, 0, st>>>(idx, m, rp, pp);
       note_launches(1);
-      if (r) break;
       S.rk4_particle_steps += rk;
     }
     cudaEventRecord(e2, st);
