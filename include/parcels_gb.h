@@ -222,7 +222,7 @@ PG_API pg_status pg_fieldset_load_snapshot(pg_fieldset *fs, int s, const void *d
 
 /* Stream snapshots instead of keeping them all resident: the library keeps
  * a ring of device slots (four unless pg_fieldset_set_ring says otherwise)
- * and, during pg_execute, uploads the next snapshot on its own side stream
+ * and, during pg_execute, uploads the next snapshots on its own side stream
  * while the current ones are in use.  Source: either `ptrs`
  * (nt host or device pointers, each valid for the lifetime of the field
  * set), or `cb` (called with a pinned host buffer to fill).  Exactly one of
@@ -234,8 +234,10 @@ PG_API pg_status pg_fieldset_stream(pg_fieldset *fs, const void *const *ptrs, pg
  * device slots of one snapshot each, 4 (default: two snapshots in use by a
  * launch, the third for steps that reach past its end, the next one
  * uploading; the three time slices of Sect. 3 plus the prefetch) to 64.  A
- * launch spans at most slots - 4 snapshot times after the next one, so larger
- * rings allow longer launches at slots x (snapshot bytes) of device memory. */
+ * launch spans at most B = (slots - 4) / 2 snapshot times after the next one
+ * and holds B + 3 slots; the others prefetch the snapshots that follow, in
+ * order, so larger rings allow longer launches, at slots x (snapshot bytes)
+ * of device memory, without waiting for uploads. */
 PG_API pg_status pg_fieldset_set_ring(pg_fieldset *fs, int slots);
 
 /* Device bytes held by the field set's snapshot storage. */
@@ -542,6 +544,14 @@ PG_API pg_status pg_launch_count(int64_t *count);
  * has allocated `bytes` more than it holds now (negative: no limit).  Used to
  * test that a failed allocation leaves objects unchanged. */
 PG_API pg_status pg_debug_set_alloc_limit(int64_t bytes);
+
+/* Run the bounded mbarrier wait of the tcgen05 kernels (the MLP products and
+ * the fused inference) on a barrier phase that nothing completes, with no
+ * copy or product in flight: the wait gives up after `polls` polls (1 to
+ * 1e7), the kernel records it and the call returns PG_ERR_TIMEOUT, as those
+ * kernels report a product or copy that never signals; the context stays
+ * usable.  Used to test the failure path without faulting the GPU. */
+PG_API pg_status pg_debug_bounded_wait(int64_t polls, void *stream);
 
 #ifdef __cplusplus
 }

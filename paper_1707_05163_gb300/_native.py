@@ -102,6 +102,7 @@ _SIGS = {
     "pg_pset_restore": ([_P, C.c_char_p, C.POINTER(_P)], C.c_int),
     "pg_pset_destroy": ([_P], C.c_int),
     "pg_debug_set_alloc_limit": ([C.c_int64], C.c_int),
+    "pg_debug_bounded_wait": ([C.c_int64, C.c_void_p], C.c_int),
     "pg_pset_kernel_timing": ([_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
     "pg_launch_count": ([C.POINTER(C.c_int64)], C.c_int),
     "pg_measure_l2_read": ([C.c_size_t, C.c_int, C.POINTER(C.c_double), _P], C.c_int),

@@ -367,22 +367,25 @@ pg_status upload_to_slot(pg_fieldset *fs, Slot &sl, int s) {
 }
 
 // Make the snapshots `need` resident (uploading the missing ones on the side
-// stream), then start uploading `prefetch` into a slot no chunk needs now.
-pg_status ensure_slots(pg_fieldset *fs, const std::vector<int> &need, int prefetch,
-                       cudaStream_t st) {
+// stream), then start uploading the snapshots of `prefetch`, in order, into
+// slots no chunk needs now.
+pg_status ensure_slots(pg_fieldset *fs, const std::vector<int> &need,
+                       const std::vector<int> &prefetch, cudaStream_t st) {
   auto find = [&](int s) {
     for (int q = 0; q < (int)fs->slot.size(); ++q)
       if (fs->slot[q].s == s) return q;
     return -1;
   };
-  auto needed = [&](int q) {
-    return std::find(need.begin(), need.end(), fs->slot[q].s) != need.end();
+  auto in = [](const std::vector<int> &v, int s, size_t upto) {
+    return std::find(v.begin(), v.begin() + (std::ptrdiff_t)std::min(upto, v.size()), s) !=
+           v.begin() + (std::ptrdiff_t)std::min(upto, v.size());
   };
+  auto needed = [&](int q) { return in(need, fs->slot[q].s, need.size()); };
   for (int s : need) {
     if (find(s) >= 0) continue;
     int q = -1;
     for (int c = 0; c < (int)fs->slot.size() && q < 0; ++c)
-      if (!needed(c) && fs->slot[c].s != prefetch) q = c;
+      if (!needed(c) && !in(prefetch, fs->slot[c].s, prefetch.size())) q = c;
     for (int c = 0; c < (int)fs->slot.size() && q < 0; ++c)
       if (!needed(c)) q = c;
     if (q < 0) {
@@ -402,14 +405,16 @@ pg_status ensure_slots(pg_fieldset *fs, const std::vector<int> &need, int prefet
                        sizeof(float) * fs->nfields, cudaMemcpyDeviceToDevice, st));
   }
   CU(cudaMemcpyAsync(fs->d_tab, tab.data(), sizeof(void *) * fs->nt, cudaMemcpyHostToDevice, st));
-  if (prefetch >= 0 && find(prefetch) < 0) {
+  for (size_t i = 0; i < prefetch.size(); ++i) {
+    const int s = prefetch[i];
+    if (find(s) >= 0) continue;
+    // a slot holding neither a needed snapshot nor an earlier prefetch
     int q = -1;
     for (int c = 0; c < (int)fs->slot.size() && q < 0; ++c)
-      if (!needed(c)) q = c;
-    if (q >= 0) {
-      pg_status r = upload_to_slot(fs, fs->slot[q], prefetch);
-      if (r) return r;
-    }
+      if (!needed(c) && !in(prefetch, fs->slot[c].s, i)) q = c;
+    if (q < 0) break;
+    pg_status r = upload_to_slot(fs, fs->slot[q], s);
+    if (r) return r;
   }
   return PG_OK;
 }
@@ -1391,15 +1396,18 @@ static pg_status execute_loop(pg_pset *ps, const pg_kernel *k, double runtime, d
     std::vector<int> need;
     if (fs->streaming && fs->nt == 1) {
       need.push_back(0);
-      pg_status r = ensure_slots(fs, need, -1, st);
+      pg_status r = ensure_slots(fs, need, {}, st);
       if (r) return r;
     } else if (fs->streaming) {
-      // end the chunk at most B = slots - 4 snapshot times after the next
-      // one (B = 0: at the next snapshot time); make resident the snapshots
-      // bracketing every stage time a step starting in the chunk can reach
-      // (B + 3 of them), and start uploading the one after them
+      // end the chunk at most B snapshot times after the next one (B = 0: at
+      // the next snapshot time); make resident the snapshots bracketing
+      // every stage time a step starting in the chunk can reach (B + 3 of
+      // them), and start uploading the ones after them into the other
+      // slots.  B = (slots - 4) / 2 leaves B + 1 slots for the prefetch,
+      // the snapshots the next chunk adds, so a chunk waits for no upload
+      // that the previous chunk's compute could have hidden.
       const long long m = snap_counter(fs, tc);
-      const long long B = (long long)fs->slot.size() - 4;
+      const long long B = ((long long)fs->slot.size() - 4) / 2;
       if (sgn > 0) {
         clip(snap_time(fs, m + 1 + B));
       } else {
@@ -1415,9 +1423,17 @@ static pg_status execute_loop(pg_pset *ps, const pg_kernel *k, double runtime, d
         const int s = snap_of(fs, q);
         if (std::find(need.begin(), need.end(), s) == need.end()) need.push_back(s);
       }
-      const long long pq = sgn > 0 ? q_hi + 1 : q_lo - 1;
-      int pre = -1;
-      if (fs->period > 0.0 || (pq >= 0 && pq < fs->nt)) pre = snap_of(fs, pq);
+      std::vector<int> pre;
+      const long long npre = (long long)fs->slot.size() - (long long)need.size();
+      for (long long d = 1; d <= npre; ++d) {
+        const long long pq = sgn > 0 ? q_hi + d : q_lo - d;
+        if (fs->period <= 0.0 && (pq < 0 || pq >= fs->nt)) break;
+        const int s = snap_of(fs, pq);
+        if (std::find(need.begin(), need.end(), s) != need.end() ||
+            std::find(pre.begin(), pre.end(), s) != pre.end())
+          break;
+        pre.push_back(s);
+      }
       pg_status r = ensure_slots(fs, need, pre, st);
       if (r) return r;
     }

@@ -380,6 +380,9 @@ cudaError_t mlp_fused_pack(const __nv_bfloat16 *const w[5], uint8_t *out, cudaSt
 cudaError_t mlp_fused_forward(const float *x, int64_t M, int n_in, const uint8_t *wpk,
                               const float *const bias[5], float *y, int n_out, cudaStream_t st,
                               int *err);
+cudaError_t mlp_fused_step_launch(const SurrogateStepIO &io, const uint8_t *wpk,
+                                  const float *const bias[5], cudaStream_t st, int *err);
+cudaError_t mlp_wait_probe(long long polls, int *err, cudaStream_t st);
 cudaError_t gemm_tn_splitk_tc(const __nv_bfloat16 *A, int64_t lda, int Mrows,
                               const __nv_bfloat16 *B, int64_t ldb, int N, int64_t K, float *out,
                               float *scratch, size_t scratch_bytes, cudaStream_t st, int *err);
@@ -544,6 +547,44 @@ int round64(int x) { return (x + 63) / 64 * 64; }
     }                                                                                 \
   } while (0)
 
+namespace pg {
+
+// The fused kernel's shape: inputs padded to 64, four hidden layers of 256,
+// outputs padded to 64 with at most 16 real ones.
+static bool fused_shape(const pg_mlp *n) {
+  return n->use_tc && n->fused && n->pin == 64 && n->width == 256 && n->depth == 4 &&
+         n->pout == 64 && n->n_out <= 16;
+}
+
+static cudaError_t ensure_packed(pg_mlp *n, cudaStream_t st) {
+  if (n->wpk_valid) return cudaSuccess;
+  const __nv_bfloat16 *w[5];
+  for (int l = 0; l < 5; ++l) w[l] = n->wb + n->woff[l];
+  cudaError_t e = mlp_fused_pack(w, n->wpk, st);
+  if (e == cudaSuccess) n->wpk_valid = true;
+  return e;
+}
+
+bool mlp_fused_step_ok(const pg_mlp *n) { return n && fused_shape(n) && n->n_in == 37 && n->n_out == 3; }
+
+pg_status mlp_fused_step(pg_mlp *n, const SurrogateStepIO &io, cudaStream_t st) {
+  if (!mlp_fused_step_ok(n)) { set_error("network cannot run the fused step"); return PG_ERR_ARG; }
+  CUM(ensure_packed(n, st));
+  const float *bias[5];
+  for (int l = 0; l < 5; ++l) bias[l] = n->w + n->boff[l];
+  CUM(cudaMemsetAsync(io.ferr, 0, 4, st));
+  CUM(mlp_fused_step_launch(io, n->wpk, bias, st, n->d_err));
+  int err[2] = {0, 0};
+  CUM(cudaMemcpyAsync(&err[0], n->d_err, 4, cudaMemcpyDeviceToHost, st));
+  CUM(cudaMemcpyAsync(&err[1], io.ferr, 4, cudaMemcpyDeviceToHost, st));
+  CUM(cudaStreamSynchronize(st));
+  if (err[0]) { set_error("tcgen05 product gave up waiting for its accumulator"); return PG_ERR_TIMEOUT; }
+  if (err[1]) { set_error("feature gather recorded internal error %d", err[1]); return PG_ERR_DEVICE; }
+  return PG_OK;
+}
+
+}  // namespace pg
+
 extern "C" {
 
 pg_status pg_mlp_create(int n_in, int width, int depth, int n_out, uint64_t seed, pg_mlp **out) {
@@ -669,14 +710,8 @@ pg_status pg_mlp_forward(pg_mlp *n, const float *x, int64_t M, float *y, void *s
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t chunk = 1 << 20;
   // the surrogate's shape runs as one fused tcgen05 kernel (activations on chip)
-  const bool fused = n->use_tc && n->fused && n->pin == 64 && n->width == 256 && n->depth == 4 &&
-                     n->pout == 64 && n->n_out <= 16;
-  if (fused && !n->wpk_valid) {
-    const __nv_bfloat16 *w[5];
-    for (int l = 0; l < 5; ++l) w[l] = n->wb + n->woff[l];
-    CUM(mlp_fused_pack(w, n->wpk, st));
-    n->wpk_valid = true;
-  }
+  const bool fused = fused_shape(n);
+  if (fused) CUM(ensure_packed(n, st));
   if (fused) {
     // one launch over all rows: the kernel reads the FP32 features itself
     // and needs no workspace
@@ -771,6 +806,28 @@ pg_status pg_mlp_train_step(pg_mlp *n, const float *x, const float *t, int64_t M
   adam_kernel<<<grid1((int64_t)n->nparam), 256, 0, st>>>(a);
   note_launches(1);
   CUM(refresh_bf16(n, st));
+  return PG_OK;
+}
+
+// The bounded mbarrier wait of the tcgen05 kernels, run on a phase nothing
+// completes (test hook).
+pg_status pg_debug_bounded_wait(int64_t polls, void *stream) {
+  clear_error();
+  if (polls < 1 || polls > 10000000) { set_error("invalid argument: polls in [1, 1e7]"); return PG_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  int *d = nullptr;
+  CUM(dev_alloc((void **)&d, 4));
+  int h = 0;
+  cudaError_t e = cudaMemsetAsync(d, 0, 4, st);
+  if (e == cudaSuccess) e = mlp_wait_probe((long long)polls, d, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dev_free(d);
+  CUM(e);
+  if (h) {
+    set_error("bounded wait gave up after %lld polls", (long long)polls);
+    return PG_ERR_TIMEOUT;
+  }
   return PG_OK;
 }
 

@@ -53,6 +53,7 @@
 #include <algorithm>
 
 #include "pg_host.h"
+#include "surrogate_features.cuh"
 
 namespace pg {
 
@@ -62,9 +63,11 @@ constexpr int TMF = 128;                       // rows per tile
 constexpr int kEpiWarps = 16;                  // epilogue warps (a multiple of 4)
 constexpr int kCopyWarp = kEpiWarps;
 constexpr int kMmaWarp = kEpiWarps + 1;
-constexpr int kInWarp0 = kEpiWarps + 2;        // input conversion warps
-constexpr int kInWarps = 2;
-constexpr int kFThreads = 32 * (kEpiWarps + 2 + kInWarps);
+constexpr int kInWarp0 = kEpiWarps + 2;        // input warps follow the copy and MMA warps
+// input warps: two convert feature rows (inference); four gather the
+// features of a network step, which wait on field loads
+template <bool STEP> struct InWarps { static constexpr int n = STEP ? 4 : 2; };
+template <bool STEP> __host__ __device__ constexpr int threads_of() { return 32 * (kEpiWarps + 2 + InWarps<STEP>::n); }
 constexpr int kColsPerWarp = 128 / (kEpiWarps / 4);   // of a 128-column half
 constexpr long long kFSpin = 4000000;          // mbarrier polls before giving up
 constexpr uint32_t kSuspendNs = 500;           // suspend-time hint of a poll
@@ -129,11 +132,12 @@ __device__ __forceinline__ float gelu2_f(float x) {
 }
 
 // Poll phase `parity` of an mbarrier: true once it has completed; false
-// after kFSpin polls, or (fail != nullptr) once *fail is set.  Each poll may
+// after `limit` polls, or (fail != nullptr) once *fail is set.  Each poll may
 // suspend the thread for up to kSuspendNs until the phase completes, so a
 // waiting warp takes few issue slots from the working ones.
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, const volatile int *fail) {
-  for (long long spins = 0; spins < kFSpin; ++spins) {
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, const volatile int *fail,
+                                         long long limit = kFSpin) {
+  for (long long spins = 0; spins < limit; ++spins) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
@@ -218,8 +222,9 @@ __host__ __device__ __forceinline__ Piece piece_of(int p) {
 }
 
 struct FusedArgs {
-  const float *x;               // [M x n_in] FP32 features, row-major
+  const float *x;               // [M x n_in] FP32 features, row-major (inference)
   int n_in;                     // <= 64
+  SurrogateStepIO io;           // the particles (network step)
   const uint8_t *wpk;           // packed weight pieces, 32 KB each
   const float *bias[5];         // per layer, N floats
   float *y;                     // [M x n_out] FP32
@@ -257,7 +262,39 @@ __device__ __forceinline__ void load_input_row(const FusedArgs &a, int64_t m, ui
   }
 }
 
-__global__ void __launch_bounds__(kFThreads, 1) mlp_fused_kernel(const __grid_constant__ FusedArgs a) {
+// Network step: the features of particle m (zero for a deleted particle or
+// m >= M) into row r of the input buffer, as load_input_row lays them out.
+__device__ __forceinline__ void feature_row(const FusedArgs &a, int64_t m, uint8_t *dst, int r) {
+  float o[kSurFeat];
+  bool ok = false;
+  if (m < a.M && a.io.status[m] == 0) {
+    const int e = surrogate_features(a.io.g, a.io.f, a.io.lon[m], a.io.lat[m], a.io.dep[m],
+                                     a.io.time[m], o);
+    if (e) atomicCAS(a.io.ferr, 0, e);
+    else ok = true;
+  }
+  uint8_t *row = dst + (r >> 3) * 1024 + (r & 7) * 16;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = c * 8 + 2 * j;
+      const float f0 = (ok && q < kSurFeat) ? o[q < kSurFeat ? q : 0] : 0.f;
+      const float f1 = (ok && q + 1 < kSurFeat) ? o[q + 1 < kSurFeat ? q + 1 : 0] : 0.f;
+      const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+      w[j] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+    *reinterpret_cast<uint4 *>(row + c * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// STEP = false: inference, y = the network on x.  STEP = true: one network
+// step of the learned flow map on the particles of a.io.
+template <bool STEP>
+__global__ void __launch_bounds__(threads_of<STEP>(), 1) mlp_fused_kernel(const __grid_constant__ FusedArgs a) {
+  constexpr int kInWarps = InWarps<STEP>::n;
+  constexpr int kFThreads = threads_of<STEP>();
   extern __shared__ __align__(1024) uint8_t smem[];
   float *sBias = reinterpret_cast<float *>(smem + kOffBias);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + kOffMisc);
@@ -330,8 +367,10 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_kernel(const __grid_co
         ok = __all_sync(0xffffffffu, wait_bar(bar(B_XFREE), (uint32_t)((i - 1) & 1), fail));
         if (!ok) break;
       }
-      for (int r = wi * 32 + lane; r < TMF; r += 32 * kInWarps)
-        load_input_row(a, tile * TMF + r, smem + kOffX, r);
+      for (int r = wi * 32 + lane; r < TMF; r += 32 * kInWarps) {
+        if constexpr (STEP) feature_row(a, tile * TMF + r, smem + kOffX, r);
+        else load_input_row(a, tile * TMF + r, smem + kOffX, r);
+      }
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       __syncwarp();
       if (lane == 0) bar_arrive(bar(B_XFULL));
@@ -490,10 +529,28 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_kernel(const __grid_co
           }
           if (sub == 0 && r < rows) {
             const float *bias = sBias + 4 * 256;
-            float *yr = a.y + (size_t)(m0 + r) * a.n_out;
+            if constexpr (STEP) {
+              // the displacement moves the particle (surrogate_apply)
+              const int64_t m = m0 + r;
+              if (a.io.status[m] == 0) {
+                float l = a.io.lon[m], la = a.io.lat[m], d = a.io.dep[m];
+                const uint8_t st = surrogate_apply(a.io.g, l, la, d, __uint_as_float(v[0]) + bias[0],
+                                                   __uint_as_float(v[1]) + bias[1],
+                                                   __uint_as_float(v[2]) + bias[2]);
+                if (st) {
+                  a.io.status[m] = st;
+                } else {
+                  a.io.lon[m] = l; a.io.lat[m] = la; a.io.dep[m] = d;
+                  a.io.time[m] += a.io.horizon;
+                  a.io.step[m] += 1;
+                }
+              }
+            } else {
+              float *yr = a.y + (size_t)(m0 + r) * a.n_out;
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (j < a.n_out) yr[j] = __uint_as_float(v[j]) + bias[j];
+              for (int j = 0; j < 16; ++j)
+                if (j < a.n_out) yr[j] = __uint_as_float(v[j]) + bias[j];
+            }
           }
         }
       }
@@ -514,6 +571,21 @@ __global__ void __launch_bounds__(kFThreads, 1) mlp_fused_kernel(const __grid_co
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512));
   }
+}
+
+// A bounded wait on an mbarrier phase that nothing completes (no thread
+// arrives on the barrier and no copy or product is in flight): the wait of
+// the MLP kernels gives up after `polls` polls, and the block records it in
+// *err as those kernels do, then leaves.
+__global__ void wait_probe_kernel(long long polls, int *err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32f(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n");
+  }
+  __syncthreads();
+  const bool ok = wait_bar(su32f(&bar), 0u, nullptr, polls);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicCAS(err, 0, 1);
 }
 
 // Pack the BF16 weights of the five layers (W_l [dout x din] row-major, as
@@ -543,6 +615,14 @@ __global__ void pack_weights_kernel(const __nv_bfloat16 *w0, const __nv_bfloat16
 
 }  // namespace
 
+// The bounded-wait probe: one block of 128 threads; *err (device) set to 1
+// when the wait gave up.
+cudaError_t mlp_wait_probe(long long polls, int *err, cudaStream_t st) {
+  wait_probe_kernel<<<1, 128, 0, st>>>(polls, err);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 // Bytes of the packed weights of the fused forward.
 size_t mlp_fused_packed_bytes() { return (size_t)kPieces * kPieceBytes; }
 
@@ -562,8 +642,8 @@ cudaError_t mlp_fused_forward(const float *x, int64_t M, int n_in, const uint8_t
   if (M == 0) return cudaSuccess;
   if (n_out < 1 || n_out > 16 || n_in < 1 || n_in > 64 || !err || ((uintptr_t)wpk % 16))
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(mlp_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kSmem);
+  cudaError_t e = cudaFuncSetAttribute(mlp_fused_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -573,7 +653,31 @@ cudaError_t mlp_fused_forward(const float *x, int64_t M, int n_in, const uint8_t
   for (int l = 0; l < 5; ++l) a.bias[l] = bias[l];
   const int64_t ntiles = (M + TMF - 1) / TMF;
   const int grid = (int)(ntiles < sms ? ntiles : sms);
-  mlp_fused_kernel<<<grid, kFThreads, kSmem, st>>>(a);
+  mlp_fused_kernel<false><<<grid, threads_of<false>(), kSmem, st>>>(a);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// One network step of the learned flow map on io's particles (the network's
+// shape: 37 features, 4 x 256, 3 outputs); *err as for mlp_fused_forward,
+// feature errors in *io.ferr.
+cudaError_t mlp_fused_step_launch(const SurrogateStepIO &io, const uint8_t *wpk,
+                                  const float *const bias[5], cudaStream_t st, int *err) {
+  if (io.n == 0) return cudaSuccess;
+  if (!err || !io.ferr || ((uintptr_t)wpk % 16)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(mlp_fused_kernel<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  FusedArgs a;
+  a.x = nullptr; a.n_in = kSurFeat; a.io = io; a.wpk = wpk; a.y = nullptr; a.M = io.n;
+  a.n_out = 3; a.err = err;
+  for (int l = 0; l < 5; ++l) a.bias[l] = bias[l];
+  const int64_t ntiles = (io.n + TMF - 1) / TMF;
+  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  mlp_fused_kernel<true><<<grid, threads_of<true>(), kSmem, st>>>(a);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -207,6 +207,26 @@ cudaError_t launch_from_cell(const GridArgs &g, const int32_t *ci, const int32_t
 // Grid argument block of a field set (defined in capi.cu).
 GridArgs grid_args_of(const pg_fieldset *fs);
 
+// One network step of the learned flow map fused into the tcgen05 inference
+// kernel: the particles' features gathered on chip, the network, the
+// displacement applied to the particles (surrogate_features.cuh).
+struct SurrogateStepIO {
+  GridArgs g;
+  FieldArgs f;
+  float *lon, *lat, *dep;
+  double *time;
+  uint32_t *step;
+  uint8_t *status;
+  int64_t n;
+  double horizon;
+  int *ferr;                  // device word: feature error (time range, missing slab)
+};
+// Whether the network's engine and shape allow the fused step.
+bool mlp_fused_step_ok(const pg_mlp *net);
+// The fused step (weights packed first if needed); reads back the network's
+// and the features' error words.
+pg_status mlp_fused_step(pg_mlp *net, const SurrogateStepIO &io, cudaStream_t st);
+
 // Kernel argument block of a kernel on a field set: NaN parameters and those
 // of the settle and age behaviours from the field set's constants (capi.cu).
 pg_status resolve_kernel(const pg_kernel *k, const pg_fieldset *fs, uint64_t seed, KernArgs &a);

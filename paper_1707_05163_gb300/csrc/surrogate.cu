@@ -1,30 +1,20 @@
 // surrogate.cu -- the learned 24-hour flow map: features, displacement,
 // and the run loop in which RK4 (Sect. 2.1.1) checks the network and takes
-// over for the particles it rejects.
-//
-// Features of a particle at time t (37 floats):
-//   0 xi, 1 eta       position inside its lon / lat cell, in [0, 1]
-//   2 lat / 90, 3 depth / 1000 m, 4 phase of the field's period in [0, 1)
-//   5..36             U and V / 0.3 m/s at the 4 x 4 nodes around the cell
-//                     (i-1..i+2, j-1..j+2), interpolated linearly in depth
-//                     and in time to the particle's depth and time
-// Output (3 floats): displacement over the horizon in cells of lon and lat,
-// and in units of 100 m of depth.
+// over for the particles it rejects.  The features and the displacement are
+// those of surrogate_features.cuh.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <vector>
 
-#include "advect_common.cuh"
+#include "surrogate_features.cuh"
 #include "pg_host.h"
 
 namespace pg {
 
 namespace {
 
-constexpr int kFeat = 37;
-constexpr float kVelScale = 1.0f / 0.3f;
-constexpr float kDepthUnit = 100.0f;
+constexpr int kFeat = kSurFeat;
 
 __device__ __forceinline__ int find_cell(const float *x, int n, float p) {
   int lo = 0, hi = n - 1;
@@ -41,74 +31,19 @@ __global__ void features_kernel(GridArgs g, FieldArgs f, const float *lon, const
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     float *o = out + p * kFeat;
+    float v[kFeat];
     if (status[p] != 0) {
+#pragma unroll
       for (int q = 0; q < kFeat; ++q) o[q] = 0.f;
       continue;
     }
-    // cell and fractions
-    float q = wrap_lon(lon[p], g.lonf[0]);
-    int i;
-    float xi;
-    if (q >= g.lonf[g.nx - 1]) {
-      i = g.nx - 1;
-      xi = (q - g.lonf[g.nx - 1]) / (g.lon_end_f - g.lonf[g.nx - 1]);
-    } else {
-      i = axis_search<float>(g, 0, g.nx, q);
-      xi = (q - g.lonf[i]) / (g.lonf[i + 1] - g.lonf[i]);
-    }
-    const float y = fminf(fmaxf(lat[p], g.latf[0]), g.latf[g.ny - 1]);
-    const int j = axis_search<float>(g, 1, g.ny, y);
-    const float eta = (y - g.latf[j]) / (g.latf[j + 1] - g.latf[j]);
-    int k = 0;
-    float zeta = 0.f;
-    if (g.nz > 1) {
-      const float z = fminf(fmaxf(dep[p], g.depthf[0]), g.depthf[g.nz - 1]);
-      k = axis_search<float>(g, 2, g.nz, z);
-      zeta = (z - g.depthf[k]) / (g.depthf[k + 1] - g.depthf[k]);
-    }
-    // time interval
-    int s0 = 0, s1 = 0;
-    float tau = 0.f, phase = 0.f;
-    if (f.nt > 1) {
-      double tt, ta, tb;
-      int a0 = -1, a1 = -1;
-      if (!time_interval(f, time[p], a0, a1, tt, ta, tb)) {
-        atomicCAS(err, 0, (int)DEVERR_TIME_RANGE);
-        continue;
-      }
-      s0 = a0; s1 = a1;
-      tau = (float)((tt - ta) / (tb - ta));
-      if (f.period > 0.0) phase = (float)((tt - f.times[0]) / f.period);
-    }
-    const float *S0 = reinterpret_cast<const float *>(f.tab[s0]);
-    const float *S1 = reinterpret_cast<const float *>(f.tab[s1]);
-    if (!S0 || !S1) {
-      atomicCAS(err, 0, (int)DEVERR_SLAB_MISSING);
+    const int r = surrogate_features(g, f, lon[p], lat[p], dep[p], time[p], v);
+    if (r) {
+      atomicCAS(err, 0, r);
       continue;
     }
-    const int stride = f.nf == 2 ? 2 : 4;
-    o[0] = xi; o[1] = eta; o[2] = lat[p] * (1.0f / 90.0f); o[3] = dep[p] * 1e-3f; o[4] = phase;
-    int q2 = 5;
-    for (int dj = -1; dj <= 2; ++dj) {
-      const int jj = min(max(j + dj, 0), g.ny - 1);
-      for (int di = -1; di <= 2; ++di) {
-        int ii = i + di;
-        if (ii < 0) ii += g.nx;
-        if (ii >= g.nx) ii -= g.nx;
-        // U and V of a node are adjacent in the slab: one 8-byte load per
-        // node, level and snapshot
-        const size_t n0 = (((size_t)k * g.ny + jj) * g.nx + ii) * stride;
-        const size_t n1 = g.nz > 1 ? n0 + (size_t)g.ny * g.nx * stride : n0;
-        const float2 a0 = __ldg(reinterpret_cast<const float2 *>(S0 + n0));
-        const float2 a1 = __ldg(reinterpret_cast<const float2 *>(S0 + n1));
-        const float2 b0 = __ldg(reinterpret_cast<const float2 *>(S1 + n0));
-        const float2 b1 = __ldg(reinterpret_cast<const float2 *>(S1 + n1));
-        const float au = a0.x + (a1.x - a0.x) * zeta, bu = b0.x + (b1.x - b0.x) * zeta;
-        const float av = a0.y + (a1.y - a0.y) * zeta, bv = b0.y + (b1.y - b0.y) * zeta;
-        o[q2++] = (au + (bu - au) * tau) * kVelScale;
-        o[q2++] = (av + (bv - av) * tau) * kVelScale;
-      }
-    }
+#pragma unroll
+    for (int q = 0; q < kFeat; ++q) o[q] = v[q];
   }
 }
 
@@ -119,17 +54,10 @@ __global__ void apply_kernel(GridArgs g, float *lon, float *lat, float *dep, dou
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     if (status[p] != 0) continue;
-    float nl = lon[p] + y[p * 3 + 0] * g.df[0];
-    const float na = lat[p] + y[p * 3 + 1] * g.df[1];
-    const float nd = dep[p] + y[p * 3 + 2] * kDepthUnit;
-    if (g.periodic) nl = wrap_lon(nl, g.lonf[0]);
-    uint8_t st = 0;
-    if (!g.periodic && !(nl >= g.lonf[0] && nl <= g.lonf[g.nx - 1])) st = 1;
-    else if (!(na >= g.latf[0] && na <= g.latf[g.ny - 1])) st = 1;
-    else if (g.nz > 1 && !(nd >= g.depthf[0] && nd <= g.depthf[g.nz - 1])) st = 2;
-    else if (!(nl == nl)) st = 3;
+    float l = lon[p], a = lat[p], d = dep[p];
+    const uint8_t st = surrogate_apply(g, l, a, d, y[p * 3 + 0], y[p * 3 + 1], y[p * 3 + 2]);
     if (st) { status[p] = st; continue; }
-    lon[p] = nl; lat[p] = na; dep[p] = nd;
+    lon[p] = l; lat[p] = a; dep[p] = d;
     time[p] += horizon;
     step[p] += 1;
   }
@@ -149,7 +77,7 @@ __global__ void displacement_kernel(GridArgs g, const float *lon0, const float *
     }
     y[p * 3 + 0] = dl / g.df[0];
     y[p * 3 + 1] = (lat1[p] - lat0[p]) / g.df[1];
-    y[p * 3 + 2] = (dep1[p] - dep0[p]) / kDepthUnit;
+    y[p * 3 + 2] = (dep1[p] - dep0[p]) / kSurDepthUnit;
   }
 }
 
@@ -441,7 +369,21 @@ pg_status pg_surrogate_run(pg_pset *ps, pg_mlp *net, const pg_kernel *k, int nst
     dst->t_max = src->t_max;
     return q;
   };
+  // a network step: features, network, displacement -- one fused tcgen05
+  // kernel for the surrogate's network shape, else three kernels
+  const bool fused_step = mlp_fused_step_ok(net);
   auto network_step = [&]() -> pg_status {
+    if (fused_step) {
+      SurrogateStepIO io;
+      io.g = grid_args_of(ps->fs);
+      io.f = field_args(ps->fs);
+      io.lon = (float *)ps->x; io.lat = (float *)ps->y; io.dep = (float *)ps->z;
+      io.time = ps->time; io.step = ps->step; io.status = ps->status;
+      io.n = ps->n; io.horizon = horizon; io.ferr = ps->d_err;
+      const pg_status q = mlp_fused_step(net, io, st);
+      if (!q) { ps->t_min += horizon; ps->t_max += horizon; }
+      return q;
+    }
     pg_status q = pg_surrogate_features(ps, x, st);
     if (!q) q = pg_mlp_forward(net, x, n, y, st);
     if (!q) q = pg_surrogate_apply(ps, y, horizon, st);

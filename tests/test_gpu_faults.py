@@ -4,7 +4,8 @@ hook), and each call must return PG_ERR_NOMEM and leave its objects as they
 were (the error conventions of the C ABI; the paper's recovery kernels,
 Sect. 2.1.2, cover particle errors, these cover the library's own).  Plus
 quantised storage of fields with NaN nodes (land): the scale ignores NaN,
-as the oracle's does."""
+as the oracle's does; and the bounded device wait of the tcgen05 kernels
+running out on a barrier nothing completes."""
 import numpy as np
 import pytest
 
@@ -138,3 +139,25 @@ def test_quantised_field_with_nan_nodes(pg, storage, kind):
     assert (st == 3).sum() > 100
     assert np.mean(g["final"]["status"] == st) > 0.99
     assert (g["final"]["status"][st == 3] == 3).mean() > 0.99
+
+
+def test_bounded_wait_gives_up_and_reports_timeout(pg):
+    """The bounded mbarrier wait of the tcgen05 kernels, run on a barrier
+    phase that nothing completes (no copy or product in flight), gives up
+    after its poll limit; the kernel records it, the call returns
+    PG_ERR_TIMEOUT with its message, and the context stays usable: the fused
+    tcgen05 forward runs afterwards and matches the layer-by-layer one."""
+    import torch
+    lib = pg.load()
+    for polls in (1, 1000, 100_000):
+        assert lib.pg_debug_bounded_wait(polls, None) == -6
+        assert b"gave up" in lib.pg_last_error()
+    assert lib.pg_debug_bounded_wait(0, None) == -1          # argument checked
+    net = pg.MLP(37, 256, 4, 3, seed=2)
+    x = torch.randn(1000, 37, device="cuda")
+    net.set_engine(1)
+    y1 = net.forward(x).cpu().numpy()
+    net.set_engine(2)
+    y2 = net.forward(x).cpu().numpy()
+    assert np.isfinite(y1).all()
+    np.testing.assert_array_equal(y1, y2)

@@ -129,3 +129,30 @@ def test_trained_network_saves_rk4_steps_within_its_threshold(env):
     dlon = (g["lon"] - r["lon"] + 180.0) % 360.0 - 180.0
     e = np.maximum(np.abs(dlon), np.abs(g["lat"] - r["lat"]))[ok] / 2.0   # 2-degree cells
     assert np.mean(e) < 0.5, np.mean(e)
+
+
+def test_fused_network_step_equals_separate_kernels(env):
+    """For the surrogate's network shape (37 features, 4 x 256, 3 outputs) a
+    network step is one fused tcgen05 kernel (features gathered on chip, the
+    network, the displacement applied); with the layer-by-layer engine it is
+    three kernels (features, network, apply).  The two compute the same
+    features, products and displacements, so whole surrogate runs -- network
+    steps, RK4 checks, rejections, re-integration -- end in the same states
+    bit for bit; 30,077 particles (235 row tiles and a ragged one)."""
+    pg, torch, spec, fs = env
+    net = pg.MLP(37, 256, 4, 3, seed=3)
+    lon, lat, dep = synth.uniform_particles(30_077, 12, (0, 360), (-70, 70), (10.0, 800.0),
+                                            dtype=np.float32)
+    K = pg.Kernel("rk4")
+    res = []
+    for engine in (1, 2):
+        net.set_engine(engine)
+        ps = pg.ParticleSet(fs, lon, lat, dep, pos="f32")
+        st = pg.surrogate_run(ps, net, K, nsteps=4, check_every=2, threshold=0.2)
+        res.append((ps.get(), st))
+    (a, sa), (b, sb) = res
+    for k in ("lon", "lat", "depth", "time", "step", "status", "id"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    assert sa["rejected"] == sb["rejected"] and sa["checked"] == sb["checked"]
+    assert 0 < sa["rejected"] < sa["checked"]          # both branches of the check ran
+    assert (a["status"] == 0).mean() > 0.5
