@@ -50,8 +50,9 @@ def parse():
     ap.add_argument("--resort-steps", type=int, default=288)
     ap.add_argument("--chunk-steps", type=int, default=288)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-ring", type=int, default=4,
-                    help="snapshot ring slots of the end-to-end leg (4: two in use + the next)")
+    ap.add_argument("--e2e-ring", type=int, default=8,
+                    help="snapshot ring slots of the end-to-end leg (4: two in use + the next; "
+                         "8: three-day launches, five in use + the next three)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mlp", action="store_true",
                     help="skip the surrogate network's inference timing in the 3-D line")
@@ -367,13 +368,15 @@ def main():
     elapsed_ms, total_all = reduce_over_ranks(elapsed_ms, total_steps, dev)
     value = total_all / (elapsed_ms / 1e3)
 
-    # the field streamed from pinned host memory (two snapshots in use plus
-    # the next one uploading): device-timed with particles on the device, and
-    # end to end through the C ABI from host buffers
+    # the field streamed from pinned host memory (4 slots: two snapshots in
+    # use plus the next one uploading; 8 slots: three-day launches):
+    # device-timed with particles on the device, and end to end through the
+    # C ABI from host buffers
     e2e, streamed = None, None
     if not args.no_e2e and host_field is not None:
         streamed = {f"ring{r}": streamed_leg(pg, gf, torch, host_field, lon, lat, dep, kern,
-                                             runtime, args, r, False) for r in (4,)}
+                                             runtime, args, r, False)
+                    for r in sorted({4, args.e2e_ring})}
         e2e = streamed_leg(pg, gf, torch, host_field, lon, lat, dep, kern, runtime, args,
                            args.e2e_ring, True)
 
@@ -515,7 +518,8 @@ def streamed_leg(pg, gf, torch, host_field, lon, lat, dep, kern, runtime, args, 
     """The workload with its snapshots streamed from pinned host memory
     through a ring of `ring` device slots (4: two snapshots in use by a
     launch, one for steps that reach past it, the next uploading; launches
-    end at the next snapshot time).  from_host: particles uploaded from
+    end at the next snapshot time; larger rings: launches of (ring - 4) / 2
+    + 1 days, the spare slots prefetching).  from_host: particles uploaded from
     pinned FP64 host arrays and the final state read back into them, all
     inside the timed region (the end-to-end number); otherwise particles
     start on the device and only the execute is timed (CUDA events).

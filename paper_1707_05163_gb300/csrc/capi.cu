@@ -705,7 +705,12 @@ pg_status pg_fieldset_stream(pg_fieldset *fs, const void *const *ptrs, pg_snapsh
   }
   if (e == cudaSuccess && fs->stage_bytes < bytes) e = dev_alloc(&stage, bytes);
   if (e == cudaSuccess && cb) e = cudaMallocHost(&pinned, bytes);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+  // the side stream at the highest priority: its repack kernel then takes
+  // SM slots as the advection kernel's blocks retire, instead of waiting
+  // for the whole launch, and the next copy into the staging buffer follows
+  int prio_lo = 0, prio_hi = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_hi);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&stage_free, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(stage_free, side);
   if (e != cudaSuccess) {
