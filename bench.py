@@ -1062,15 +1062,38 @@ def precision_workload(args, rank, world, local):
     errs = {}
     ospec = dict(lon=gf.lon, lat=gf.lat, depth=np.zeros(1), times=gf.times)
 
+    # error against time: the state at these days (the last one the horizon)
+    stops = [d for d in (1.0, 7.0, 30.0) if d < days] + [days]
+
     def oracle_final(data):
+        """The oracle on the first `sub` particles; returns the state at each
+        stop (the last one is the final state) and its particle-steps/s."""
         f = O.Field(gf.lon, gf.lat, np.zeros(1), gf.times, data, 1, True, gf.period)
         st = [np.array(lon[:sub], np.float64), np.array(lat[:sub], np.float64), np.zeros(sub),
               np.zeros(sub), np.arange(sub, dtype=np.uint64), np.zeros(sub, np.uint32),
               np.zeros(sub, np.uint8)]
         t0 = time.perf_counter()
-        done = O.run(f, O.Kernel(O.RK4, O.BROWNIAN, K, 0.0, 3), *st, 3600.0, runtime, runtime,
-                     nthreads=cores)
-        return st, done / (time.perf_counter() - t0)
+        done = 0
+        at = {}
+        for d in stops:
+            done += O.run(f, O.Kernel(O.RK4, O.BROWNIAN, K, 0.0, 3), *st, 3600.0, d * DAY, runtime,
+                          nthreads=cores)
+            at[d] = [a.copy() for a in st]
+        return at, done / (time.perf_counter() - t0)
+
+    def gpu_at_stops(fs, pos):
+        """The same form run again with stops (launch boundaries do not change
+        FP32 results); the first `sub` particles' state at each stop."""
+        ps = pg.ParticleSet(fs, dl, da, pos=pos, seed=3)
+        ps.set_tune(args.block, args.resort_steps, 24)
+        out, t = {}, 0.0
+        for d in stops:
+            ps.execute(kern, d * DAY - t, 3600.0)
+            t = d * DAY
+            g = ps.get()
+            out[d] = {k: v[:sub] for k, v in g.items()}
+        ps.destroy()
+        return out
 
     def err_cells(g, st):
         ok = (st[6] == 0) & (g["status"] == 0)
@@ -1080,12 +1103,20 @@ def precision_workload(args, rank, world, local):
         return {"mean": float(np.mean(e[ok])), "max": float(np.max(e[ok])),
                 "status_equal": bool((st[6] == g["status"]).all())}
 
-    st_q, orate = oracle_final(hostq)
-    st_32, _ = oracle_final(host32)
+    at_q, orate = oracle_final(hostq)
+    at_32, _ = oracle_final(host32)
+    st_q, st_32 = at_q[days], at_32[days]
     qname = "cell_" + args.storage
     errs[qname + "_vs_oracle_same_field"] = err_cells(finals[qname], st_q)
     errs[qname + "_vs_oracle_fp32_field"] = err_cells(finals[qname], st_32)
     errs["plain_f32_vs_oracle_fp32_field"] = err_cells(finals["plain_f32"], st_32)
+    gq, g32 = gpu_at_stops(fs_q, "cell"), gpu_at_stops(fs_32, "f32")
+    errs_vs_time = {
+        f"{d:g}_days": {
+            qname + "_vs_oracle_same_field": err_cells(gq[d], at_q[d])["mean"],
+            qname + "_vs_oracle_fp32_field": err_cells(gq[d], at_32[d])["mean"],
+            "plain_f32_vs_oracle_fp32_field": err_cells(g32[d], at_32[d])["mean"]}
+        for d in stops}
     # diffusion variance against 2 K t on a zero-velocity copy of the grid
     fz = pg.FieldSet(gf.lon, gf.lat, None, mesh="spherical", periodic_lon=True, nfields=2,
                      storage=args.storage)
@@ -1108,6 +1139,7 @@ def precision_workload(args, rank, world, local):
                                f"particles, dt 1 h, {days:g} days", "form": "cell index + FP32 offset"},
         "plain_fp32_rate": rates["plain_f32"], "speedup_vs_plain_fp32": rates[qname] / rates["plain_f32"],
         "error_cells": errs,
+        "mean_error_cells_vs_time": errs_vs_time,
         "diffusion_variance_over_2Kt_1day": {"lat": var_lat / (2 * K * DAY),
                                              "lon_at_equator": var_lon / (2 * K * DAY), "n": nb},
         "cpu_baseline": {"value": orate, "unit": UNIT, "cores": cores, "kind": "oracle",
