@@ -1,14 +1,19 @@
 // mlp_fused.cu -- the surrogate network's inference forward in one kernel on
-// the 5th-generation tensor cores, activations kept on chip.
+// the 5th-generation tensor cores, activations kept on chip; and, in a
+// second instance of the same kernel, a whole network step of the learned
+// flow map (features gathered from the field, the network, the displacement
+// applied to the particles).
 //
 // Network: 64 (padded input) -> 256 -> 256 -> 256 -> 256 -> n_out (<= 16;
 // the weights are padded to 64 outputs), GELU after the hidden layers (the
 // shapes of the flow-map surrogate).  One persistent CTA per SM walks
-// 128-row tiles with three kinds of warps working at the same time:
+// 128-row tiles with four kinds of warps working at the same time:
 //
-//   * two input warps convert each tile's FP32 feature rows into BF16 in the
-//     operand layout of shared memory (zero-padded to 64 columns) once the
-//     previous tile's first layer has read the buffer;
+//   * input warps fill the tile's input buffer once the previous tile's
+//     first layer has read it: two convert FP32 feature rows into BF16 in the
+//     operand layout of shared memory (zero-padded to 64 columns); in the
+//     network step four gather each particle's 37 features from the field
+//     (surrogate_features.cuh), whose loads they wait on;
 //   * one lane of a copy warp streams, for every tile, fourteen 32 KB weight
 //     pieces -- layer 0; layers 1-3 as four K-quarters each; layer 4 -- into
 //     a ring of four slots, each copy completing on the slot's "full"
@@ -22,7 +27,8 @@
 //     group share the columns), add the bias, apply GELU and write BF16
 //     activations into shared memory in the operand layout of the next
 //     product; the last layer's 16 columns (plus bias) go to global memory
-//     in FP32.
+//     in FP32, or, in the network step, move the particles
+//     (surrogate_apply).
 //
 // The epilogue stores 2 GELU(x) = x (1 + t), one multiply per element fewer
 // than GELU(x) = h + h t with h = x / 2, and the packed weights of layers 1-4
