@@ -116,11 +116,12 @@ def test_backward_in_time_fp32_and_cell(pg, form, chunk):
     _outputs(g, o, spec, f"{form} chunk {chunk}")
 
 
-@pytest.mark.parametrize("ring", [4, 7])
+@pytest.mark.parametrize("ring", [4, 7, 10])
 def test_backward_streamed_equals_resident(pg, ring):
     """Backward in time with snapshots streamed through the ring (four slots:
-    one-day launches; seven: launches spanning up to four snapshot times)
-    equals the resident field bit for bit."""
+    one-day launches; seven: launches spanning up to two snapshot times, the
+    spare slots prefetching; ten: up to four) equals the resident field bit
+    for bit."""
     spec = _global(nz=8, nt=5)
     lon, lat, dep = synth.uniform_particles(2000, 19, (0, 360), (-70, 70), (6.0, 900.0),
                                             dtype=np.float32)

@@ -322,7 +322,8 @@ def test_streamed_equals_resident(pg):
             else:
                 fs.stream(callback=lambda s, out: out.__setitem__(Ellipsis, spec.data[s]))
         ps = pg.ParticleSet(fs, lon, lat, dep, pos="f32")
-        if mode == "ring6":       # launches of up to three days across snapshot times
+        if mode == "ring6":       # launches of up to two days across snapshot times, two
+                                  # snapshots prefetched
             ps.set_tune(block=128, resort_steps=0, chunk_steps=200)
         res.append(gpu_run(ps, pg.Kernel("rk4"), T, 1800.0, 2.25 * DAY if mode == "ring6" else DAY))
     for r in res[1:]:
