@@ -50,9 +50,10 @@ def parse():
     ap.add_argument("--resort-steps", type=int, default=288)
     ap.add_argument("--chunk-steps", type=int, default=288)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-ring", type=int, default=8,
+    ap.add_argument("--e2e-ring", type=int, default=16,
                     help="snapshot ring slots of the end-to-end leg (4: two in use + the next; "
-                         "8: three-day launches, five in use + the next three)")
+                         "8: three-day launches; 16: six-day launches, the launch length of "
+                         "the resident run)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mlp", action="store_true",
                     help="skip the surrogate network's inference timing in the 3-D line")
@@ -415,6 +416,18 @@ def main():
         hbm_view = {"bytes_per_particle_step": b, "achieved_GBps": b * kernel_rate / 1e9,
                     "peak_GBps": hbm_peak, "frac": b * kernel_rate / 1e9 / hbm_peak,
                     "peak_source": peak_kind}
+    # instruction issue: each SM issues at most one warp instruction per cycle
+    # on each of its 4 schedulers; the kernel's count per warp-step (32
+    # particle-steps) comes from the same committed capture as the bytes
+    issue_view = None
+    if cap and cap.get("warp_instructions_per_warp_step"):
+        ipps = cap["warp_instructions_per_warp_step"] / 32.0
+        ipk = sms * 4 * sm_mhz * 1e6
+        issue_view = {"warp_instructions_per_particle_step": ipps,
+                      "achieved_warp_inst_per_s": ipps * kernel_rate, "peak_warp_inst_per_s": ipk,
+                      "frac": ipps * kernel_rate / ipk,
+                      "peak_source": f"derived: {sms} SMs x 4 schedulers x 1 warp instruction "
+                                     "per cycle x max SM clock"}
     gather_gbs = ALGO_BYTES_PER_STEP * kernel_rate / 1e9
     mlp = None
     if rank == 0 and not args.no_mlp:
@@ -438,11 +451,13 @@ def main():
                      "alu_frac": achieved / fp32_peak,
                      "l2_frac": l2_view["frac"] if l2_view else None,
                      "hbm_frac": hbm_view["frac"] if hbm_view else None,
+                     "issue_frac": issue_view["frac"] if issue_view else None,
                      "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
                      "kernel": "advect_plain_kernel<float, float, 3, true, GEO_SPH_PER>",
                      "algorithmic_flops_per_particle_step": ALGO_FLOPS_PER_STEP,
                      "avg_launch_ms": avg_launch_s * 1e3, "launches": kern_launches,
-                     "l2": l2_view, "hbm": hbm_view, "l2_read_peak_GBps": l2_peak,
+                     "l2": l2_view, "hbm": hbm_view, "issue": issue_view,
+                     "l2_read_peak_GBps": l2_peak,
                      "traffic_capture": cap.get("captured") if cap else None,
                      "gather_view": {"algorithmic_bytes_per_particle_step": ALGO_BYTES_PER_STEP,
                                      "effective_GBps": gather_gbs,
