@@ -150,7 +150,8 @@ typedef struct {
 /* Tuning of the time loop.  Zero fields take defaults. */
 typedef struct {
     int block;          /* threads per block of the advection kernel (default 256)  */
-    int resort_steps;   /* Morton re-sort every this many steps (0: never)           */
+    int resort_steps;   /* Morton re-sort before the first launch of an execute and
+                           every this many steps (0: never)                          */
     int chunk_steps;    /* at most this many steps per kernel launch (default 64)    */
 } pg_tune;
 
@@ -366,10 +367,11 @@ PG_API pg_status pg_execute_records(pg_pset *ps, const pg_kernel *k, double runt
  * field set with all snapshots resident.  Every `window` seconds of
  * simulated time is one launch of a persistent kernel that walks a work list
  * of (release, tile) pairs, heaviest first.  Releases of at least 65,536
- * particles are Morton re-sorted every tune->resort_steps windows (0: never;
- * in this call the field counts windows, not steps).  tune == NULL runs the
- * autotuner: it times each block size in {64, 128, 256} with each re-sort
- * interval in {never, 1, 2} over the first (up to) four windows from a saved
+ * particles are Morton re-sorted before the first window and every
+ * tune->resort_steps windows (0: never; in this call the field counts
+ * windows, not steps).  tune == NULL runs the autotuner: it times each block
+ * size in {64, 128, 256} with each re-sort interval in {never, 1, 2, 4} over
+ * the first (up to) four windows from a saved
  * copy of the state, restores the state and keeps the fastest; with
  * `tune_cache` (a file path, may be NULL) the choice is stored under a key of
  * the GPU name and the workload's shape and reused by later calls.  The

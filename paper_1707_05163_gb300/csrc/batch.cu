@@ -99,6 +99,11 @@ cudaError_t enqueue_windows(Batch &B, int w0, int w1, int block, int resort_ever
   cudaError_t e = batch_op(b, fs->storage, block, 0, st, &bps);
   if (e != cudaSuccess) return e;
   const int grid = std::max(1, std::min(bps * fs->sm_count, B.ntiles));
+  // with re-sorting on, the first window too runs on Morton-ordered particles
+  if (resort_every > 0 && w0 == 0 && w1 > 0) {
+    for (pg_pset *p : B.ps)
+      if (p->n >= kResortMin && (e = launch_resort(p, st, nullptr)) != cudaSuccess) return e;
+  }
   for (int w = w0; w < w1; ++w) {
     b.next_tile = B.d_next + w;
     b.t_stop = B.t_begin + (double)(w + 1) * B.window;
@@ -324,7 +329,7 @@ extern "C" pg_status pg_execute_batch(int nrel, pg_pset *const *psets,
       CUB(save_state(B, bk, st));
       const int trial = std::min(B.nwin, 4);
       const int blocks[] = {64, 128, 256};
-      const int resorts[] = {0, 1, 2};
+      const int resorts[] = {0, 1, 2, 4};
       float best = 1e30f;
       cudaEvent_t e0, e1;
       CUB(cudaEventCreate(&e0));

@@ -1384,6 +1384,10 @@ static pg_status execute_loop(pg_pset *ps, const pg_kernel *k, double runtime, d
   double next_out = output_dt > 0.0 ? t_begin + sgn * output_dt : t_end;
   double next_sort = resort_len > 0.0 ? t_begin + sgn * resort_len : t_end;
   int64_t n_active = ps->n;
+  // particles arrive in the caller's order (or the order the last execute
+  // left): with re-sorting on, the first launch too gets them in Morton
+  // order, the deleted ones last (results do not depend on the order)
+  if (resort_len > 0.0 && ps->n > 0) CU(launch_resort(ps, st, &n_active));
   double tc = t_begin;
   int guard = 0;
   while (sgn * (t_end - tc) > 0.0) {
