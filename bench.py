@@ -47,7 +47,10 @@ def parse():
     ap.add_argument("--snapshots", type=int, default=30,
                     help="daily snapshots in the periodic field (30 = the workload)")
     ap.add_argument("--block", type=int, default=128)
-    ap.add_argument("--resort-steps", type=int, default=288)
+    ap.add_argument("--resort-steps", type=int, default=1440,
+                    help="Morton re-sort before the first launch of each execute and every this "
+                         "many steps (0: never); 1440: one sort per 30-day run of the 3-D "
+                         "workload (re-sorting every 288 steps as well measured 1.2 %% slower)")
     ap.add_argument("--chunk-steps", type=int, default=288)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-ring", type=int, default=16,
