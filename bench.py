@@ -1050,7 +1050,7 @@ def precision_workload(args, rank, world, local):
 
     def run(fs, pos, timed):
         ps = pg.ParticleSet(fs, dl, da, pos=pos, seed=3)
-        ps.set_tune(args.block, args.resort_steps, 24)
+        ps.set_tune(args.block, args.resort_steps, args.chunk_steps)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         steps = ps.execute(kern, runtime, 3600.0)
@@ -1103,7 +1103,7 @@ def precision_workload(args, rank, world, local):
         """The same form run again with stops (launch boundaries do not change
         FP32 results); the first `sub` particles' state at each stop."""
         ps = pg.ParticleSet(fs, dl, da, pos=pos, seed=3)
-        ps.set_tune(args.block, args.resort_steps, 24)
+        ps.set_tune(args.block, args.resort_steps, args.chunk_steps)
         out, t = {}, 0.0
         for d in stops:
             ps.execute(kern, d * DAY - t, 3600.0)
