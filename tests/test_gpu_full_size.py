@@ -1,8 +1,8 @@
 """Parity at the full size of the 3-D workload, in the launch configuration
 bench.py times: 10M particles in the upper 1000 m of a global 1/4-degree grid
 (1440 x 720 x 50, 30 daily snapshots, periodic in time and longitude), FP32
-RK4 with dt 30 min, block 128, 288-step chunks and one Morton sort before the
-first launch (re-sort interval 1440 steps).  The FP64 oracle advances a seeded sample of the same particles one by
+RK4 with dt 30 min, block 128, the 1440 steps in one launch after one Morton
+sort (chunk and re-sort interval 1440 steps).  The FP64 oracle advances a seeded sample of the same particles one by
 one through the same field.
 
 Pass/fail is at 24 h (from the same start states): mean position error below
@@ -64,7 +64,7 @@ def _gpu_and_oracle(pg, w, days):
     ps = pg.ParticleSet(w["fs"], torch.from_numpy(w["lon"]).to(w["dev"]),
                         torch.from_numpy(w["lat"]).to(w["dev"]),
                         torch.from_numpy(w["dep"]).to(w["dev"]), pos="f32", seed=0)
-    ps.set_tune(128, 1440, 288)
+    ps.set_tune(128, 1440, 1440)
     steps = ps.execute(pg.Kernel("rk4"), days * DAY, 1800.0)
     g = ps.get()
     ps.destroy()
