@@ -57,8 +57,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-ring", type=int, default=16,
                     help="snapshot ring slots of the end-to-end leg (4: two in use + the next; "
-                         "8: three-day launches; 16: six-day launches, the launch length of "
-                         "the resident run)")
+                         "8: three-day launches; 16: six-day launches)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mlp", action="store_true",
                     help="skip the surrogate network's inference timing in the 3-D line")
