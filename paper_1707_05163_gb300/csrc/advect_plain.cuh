@@ -639,13 +639,17 @@ __device__ __forceinline__ void count_steps(unsigned long long done, unsigned lo
 // FP32 3-D: at most 128 registers (two 256-thread blocks per SM); measured
 // faster than the unbounded allocation despite a few spilled words, as more
 // resident warps hide the gather and dependency latencies.  FP32 2-D: at most
-// 85 registers, six 128-thread blocks (24 warps) per SM.
+// 72 registers, seven 128-thread blocks (28 warps) per SM (1.2 % faster than six
+// on the 1/12-degree workload, a few spilled words); with the worked
+// example's behaviours, six.
 //
 // EXT = true: the FP32 kernel with the worked example's behaviours (settle,
 // age, sampled variables) and nearest-neighbour interpolation; the FP64
 // kernel always has them.
 template <typename Real, typename Store, int NF, bool D3, int GEO, bool EXT = false>
-__global__ void __launch_bounds__(sizeof(Real) == 4 && !D3 ? 128 : 256, sizeof(Real) == 4 ? (D3 ? 2 : 6) : 1) advect_plain_kernel(StepArgs a) {
+__global__ void __launch_bounds__(sizeof(Real) == 4 && !D3 ? 128 : 256,
+                                  sizeof(Real) == 4 ? (D3 ? 2 : (EXT ? 6 : 7)) : 1)
+    advect_plain_kernel(StepArgs a) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long done = 0;
   if (p < a.p.n && a.p.status[p] == 0) done = advance_particle<EXT, Real, Store, NF, D3, GEO>(a, p);
