@@ -369,9 +369,10 @@ PG_API pg_status pg_execute_records(pg_pset *ps, const pg_kernel *k, double runt
  * of (release, tile) pairs, heaviest first.  Releases of at least 65,536
  * particles are Morton re-sorted before the first window and every
  * tune->resort_steps windows (0: never; in this call the field counts
- * windows, not steps).  tune == NULL runs the autotuner: it times each block
- * size in {64, 128, 256} with each re-sort interval in {never, 1, 2, 4} over
- * the first (up to) four windows from a saved
+ * windows, not steps; an interval of at least the number of windows sorts
+ * before the first window only).  tune == NULL runs the autotuner: it times
+ * each block size in {64, 128, 256} with each re-sort interval in {never, 1,
+ * 2, 4, the whole run} over the first (up to) four windows from a saved
  * copy of the state, restores the state and keeps the fastest; with
  * `tune_cache` (a file path, may be NULL) the choice is stored under a key of
  * the GPU name and the workload's shape and reused by later calls.  The

@@ -329,7 +329,10 @@ extern "C" pg_status pg_execute_batch(int nrel, pg_pset *const *psets,
       CUB(save_state(B, bk, st));
       const int trial = std::min(B.nwin, 4);
       const int blocks[] = {64, 128, 256};
-      const int resorts[] = {0, 1, 2, 4};
+      // never; before the first window and every 1, 2 or 4 windows; before the
+      // first window only (an interval of the whole run)
+      const int last = std::max(B.nwin, 5);
+      const int resorts[] = {0, 1, 2, 4, last};
       float best = 1e30f;
       cudaEvent_t e0, e1;
       CUB(cudaEventCreate(&e0));
