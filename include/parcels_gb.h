@@ -372,7 +372,9 @@ PG_API pg_status pg_execute_records(pg_pset *ps, const pg_kernel *k, double runt
  * windows, not steps; an interval of at least the number of windows sorts
  * before the first window only).  tune == NULL runs the autotuner: it times
  * each block size in {64, 128, 256} with each re-sort interval in {never, 1,
- * 2, 4, the whole run} over the first (up to) four windows from a saved
+ * 2, 4, the whole run} over the first (up to) four windows (the sort before
+ * the first window charged at the share of the run the trial covers, as it is
+ * paid once) from a saved
  * copy of the state, restores the state and keeps the fastest; with
  * `tune_cache` (a file path, may be NULL) the choice is stored under a key of
  * the GPU name and the workload's shape and reused by later calls.  The

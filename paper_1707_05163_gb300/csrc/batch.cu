@@ -81,9 +81,18 @@ struct Batch {
   }
 };
 
-// Enqueue windows [w0, w1) with the given block size and re-sort interval.
+// Morton sort of every release large enough to gain from it.
+cudaError_t sort_releases(Batch &B, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (pg_pset *p : B.ps)
+    if (p->n >= kResortMin && (e = launch_resort(p, st, nullptr)) != cudaSuccess) return e;
+  return e;
+}
+
+// Enqueue windows [w0, w1) with the given block size and re-sort interval
+// (first_sort: with re-sorting on, sort before window 0 as well).
 cudaError_t enqueue_windows(Batch &B, int w0, int w1, int block, int resort_every,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool first_sort = true) {
   const pg_fieldset *fs = B.fs;
   BatchArgs b;
   b.g = grid_args_of(fs);
@@ -100,9 +109,8 @@ cudaError_t enqueue_windows(Batch &B, int w0, int w1, int block, int resort_ever
   if (e != cudaSuccess) return e;
   const int grid = std::max(1, std::min(bps * fs->sm_count, B.ntiles));
   // with re-sorting on, the first window too runs on Morton-ordered particles
-  if (resort_every > 0 && w0 == 0 && w1 > 0) {
-    for (pg_pset *p : B.ps)
-      if (p->n >= kResortMin && (e = launch_resort(p, st, nullptr)) != cudaSuccess) return e;
+  if (first_sort && resort_every > 0 && w0 == 0 && w1 > 0) {
+    if ((e = sort_releases(B, st)) != cudaSuccess) return e;
   }
   for (int w = w0; w < w1; ++w) {
     b.next_tile = B.d_next + w;
@@ -333,25 +341,37 @@ extern "C" pg_status pg_execute_batch(int nrel, pg_pset *const *psets,
       // first window only (an interval of the whole run)
       const int last = std::max(B.nwin, 5);
       const int resorts[] = {0, 1, 2, 4, last};
+      // The sort before the first window is paid once per run and its gain
+      // lasts the whole run, so a trial charges it at the share of the run
+      // the trial covers (trial / nwin of its time).
       float best = 1e30f;
-      cudaEvent_t e0, e1;
+      cudaEvent_t e0, e1, e2;
       CUB(cudaEventCreate(&e0));
       CUB(cudaEventCreate(&e1));
+      CUB(cudaEventCreate(&e2));
       for (int bl : blocks)
         for (int rs : resorts) {
-          if (build_tiles(bl)) { cudaEventDestroy(e0); cudaEventDestroy(e1); return PG_ERR_CUDA; }
+          if (build_tiles(bl)) {
+            cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
+            return PG_ERR_CUDA;
+          }
           CUB(restore_state(B, bk, st));
           CUB(cudaMemsetAsync(B.d_next, 0, sizeof(int) * B.nwin, st));
           CUB(cudaEventRecord(e0, st));
-          CUB(enqueue_windows(B, 0, trial, bl, rs, st));
+          if (rs > 0) CUB(sort_releases(B, st));
           CUB(cudaEventRecord(e1, st));
-          CUB(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          CUB(cudaEventElapsedTime(&ms, e0, e1));
+          CUB(enqueue_windows(B, 0, trial, bl, rs, st, false));
+          CUB(cudaEventRecord(e2, st));
+          CUB(cudaEventSynchronize(e2));
+          float ms_sort = 0.f, ms_win = 0.f;
+          CUB(cudaEventElapsedTime(&ms_sort, e0, e1));
+          CUB(cudaEventElapsedTime(&ms_win, e1, e2));
+          const float ms = ms_win + ms_sort * (float)trial / (float)B.nwin;
           if (ms < best) { best = ms; use.block = bl; use.resort_steps = rs; }
         }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
+      cudaEventDestroy(e2);
       CUB(restore_state(B, bk, st));
       CUB(cudaStreamSynchronize(st));
       write_cache(tune_cache, key, use);
