@@ -7,9 +7,10 @@
 // default) of simulated time is one launch of the persistent kernel, which
 // walks a work list of (release, tile) pairs ordered heaviest first (most
 // steps per window) with one atomic per tile, so releases of very different
-// cost balance across the SMs.  Large releases are re-sorted every k windows
-// in fixed-pointer mode so the sequence of launches is the same on every
-// replay and can be captured once.
+// cost balance across the SMs.  With re-sorting on, large releases are
+// sorted before the first window and every k windows, in fixed-pointer mode
+// so the sequence of launches is the same on every replay and can be captured
+// once.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
